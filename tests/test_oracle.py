@@ -1,0 +1,286 @@
+"""Pins for the CPU oracle: it is checked here against things other than itself.
+
+- brute force: hop distances by Boolean matrix powers on thousands of tiny graphs
+- closed forms: grid (Manhattan), path, cycle, star, complete graph, disjoint pieces
+- invariants: edge depth gap <= 1, reached set == connected component (union-find)
+- validator: accepts oracle output, rejects each kind of corrupted parent/depth
+- per-level statistics: closed forms on path and complete graphs, identities of Cascade 1
+- MLP FP64 reference: central finite differences, zero-parameter closed form, Adam step 1
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+
+def _tiny_graph(rng, n):
+    m = int(rng.integers(0, 3 * n + 1))
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    return src, dst
+
+
+def test_bfs_matches_boolean_matrix_powers_on_random_tiny_graphs():
+    rng = np.random.default_rng(20261202)
+    checked = 0
+    for g in range(10000):
+        n = int(rng.integers(1, 65)) if g % 4 else int(rng.integers(1, 9))
+        src, dst = _tiny_graph(rng, n)
+        adj = oracle.build_adjacency(n, src, dst)
+        dist = oracle.apsp_boolean(n, src, dst)
+        for s in range(n) if n <= 16 else rng.choice(n, 4, replace=False):
+            depth, parent = oracle.bfs(adj, int(s))
+            assert np.array_equal(depth, dist[s]), (g, n, s)
+            assert oracle.validate(adj, int(s), depth, parent) == 0
+            checked += 1
+    assert checked > 40000
+
+
+def test_adjacency_is_the_deduplicated_symmetric_edge_set():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        n = int(rng.integers(1, 40))
+        src, dst = _tiny_graph(rng, n)
+        adj = oracle.build_adjacency(n, src, dst)
+        pairs = set()
+        for s, d in zip(src.tolist(), dst.tolist()):
+            if s != d:
+                pairs.add((s, d))
+                pairs.add((d, s))
+        got = set()
+        for u in range(n):
+            row = adj.col[adj.row_ptr[u]:adj.row_ptr[u + 1]].tolist()
+            assert row == sorted(set(row))
+            got.update((u, v) for v in row)
+        assert got == pairs
+        assert adj.m == len(pairs)
+
+
+def test_directed_adjacency_keeps_direction():
+    src = np.array([0, 1, 1, 2, 2], np.int32)
+    dst = np.array([1, 2, 2, 0, 2], np.int32)
+    adj = oracle.build_adjacency(3, src, dst, symmetrize=False)
+    assert adj.row_ptr.tolist() == [0, 1, 2, 3]
+    assert adj.col.tolist() == [1, 2, 0]
+    depth, _ = oracle.bfs(adj, 1)
+    assert depth.tolist() == [2, 0, 1]
+
+
+def test_grid_depth_is_manhattan_distance():
+    w, h = 37, 23
+    n, src, dst = graphgen.grid(w, h, 0.0, seed=9, relabel=False)
+    adj = oracle.build_adjacency(n, src, dst)
+    rr, cc = np.divmod(np.arange(n), w)
+    for s in [0, w - 1, n - 1, (h // 2) * w + w // 3]:
+        depth, parent = oracle.bfs(adj, s)
+        sr, sc = divmod(s, w)
+        assert np.array_equal(depth, np.abs(rr - sr) + np.abs(cc - sc))
+        assert oracle.validate(adj, s, depth, parent) == 0
+
+
+def test_relabelled_grid_is_the_permuted_grid():
+    w, h = 19, 11
+    n, s0, d0 = graphgen.grid(w, h, 0.0, seed=3, relabel=False)
+    _, s1, d1 = graphgen.grid(w, h, 0.0, seed=3, relabel=True)
+    perm = graphgen.permutation(n, 3)
+    assert np.array_equal(perm[s0], s1) and np.array_equal(perm[d0], d1)
+    a0 = oracle.build_adjacency(n, s0, d0)
+    a1 = oracle.build_adjacency(n, s1, d1)
+    depth0, _ = oracle.bfs(a0, 5)
+    depth1, _ = oracle.bfs(a1, int(perm[5]))
+    assert np.array_equal(depth1[perm], depth0)
+
+
+def test_closed_forms_path_cycle_star_complete():
+    n = 50
+    i = np.arange(n)
+    path = (np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32))
+    adj = oracle.build_adjacency(n, *path)
+    for s in [0, 17, n - 1]:
+        assert np.array_equal(oracle.bfs(adj, s)[0], np.abs(i - s))
+    cyc = (np.arange(n, dtype=np.int32), ((np.arange(n) + 1) % n).astype(np.int32))
+    adj = oracle.build_adjacency(n, *cyc)
+    for s in [0, 11]:
+        d = np.abs(i - s)
+        assert np.array_equal(oracle.bfs(adj, s)[0], np.minimum(d, n - d))
+    star = (np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32))
+    adj = oracle.build_adjacency(n, *star)
+    assert np.array_equal(oracle.bfs(adj, 0)[0], np.where(i == 0, 0, 1))
+    depth, parent = oracle.bfs(adj, 7)
+    assert depth[7] == 0 and depth[0] == 1 and np.all(depth[(i != 0) & (i != 7)] == 2)
+    assert parent[7] == 7 and parent[0] == 7 and np.all(parent[(i != 0) & (i != 7)] == 0)
+    k = 12
+    comp = np.array(list(itertools.combinations(range(k), 2)), np.int32)
+    adj = oracle.build_adjacency(k, comp[:, 0], comp[:, 1])
+    assert np.array_equal(oracle.bfs(adj, 3)[0], np.where(np.arange(k) == 3, 0, 1))
+
+
+def test_disconnected_pieces_and_isolated_vertices_are_unreached():
+    src = np.array([0, 1, 4, 5, 7], np.int32)
+    dst = np.array([1, 2, 5, 6, 7], np.int32)  # 7 has only a self-loop; 3 is isolated
+    adj = oracle.build_adjacency(8, src, dst)
+    depth, parent = oracle.bfs(adj, 0)
+    assert depth.tolist() == [0, 1, 2, -1, -1, -1, -1, -1]
+    assert parent.tolist() == [0, 0, 1, -1, -1, -1, -1, -1]
+    depth, parent = oracle.bfs(adj, 7)
+    assert depth.tolist() == [-1] * 7 + [0] and parent.tolist() == [-1] * 7 + [7]
+
+
+@pytest.mark.parametrize("kind", ["rmat", "er", "ba"])
+def test_invariants_and_reached_set_equals_component(kind):
+    if kind == "rmat":
+        n, src, dst = graphgen.rmat(12, 8, seed=11)
+    elif kind == "er":
+        n, src, dst = graphgen.erdos_renyi(5000, 6000, seed=12)
+    else:
+        n, src, dst = graphgen.barabasi_albert(3000, 3, seed=13)
+    adj = oracle.build_adjacency(n, src, dst)
+    comp = oracle.components(n, src, dst)
+    for s in graphgen.sample_sources(n, src, dst, 6, seed=5):
+        depth, parent = oracle.bfs(adj, int(s))
+        assert oracle.validate(adj, int(s), depth, parent) == 0
+        reached = depth >= 0
+        assert np.array_equal(reached, comp == comp[s])
+        u = np.repeat(np.arange(n), np.diff(adj.row_ptr))
+        du, dv = depth[u], depth[adj.col]
+        both = (du >= 0) & (dv >= 0)
+        assert np.all(np.abs(du[both] - dv[both]) <= 1)
+        assert np.all((du >= 0) == (dv >= 0))
+
+
+def test_validator_rejects_corruptions():
+    n, src, dst = graphgen.rmat(10, 8, seed=21)
+    adj = oracle.build_adjacency(n, src, dst)
+    s = int(graphgen.sample_sources(n, src, dst, 1, seed=1)[0])
+    depth, parent = oracle.bfs(adj, s)
+    assert oracle.validate(adj, s, depth, parent) == 0
+    reached = np.flatnonzero((depth >= 2))
+    v = int(reached[0])
+    # parent that is not a neighbour
+    p = parent.copy()
+    nbrs = set(adj.col[adj.row_ptr[v]:adj.row_ptr[v + 1]].tolist())
+    far = next(int(x) for x in np.flatnonzero(depth == depth[v] - 1) if int(x) not in nbrs)
+    p[v] = far
+    assert oracle.validate(adj, s, depth, p) == 6
+    # parent at the wrong level (a neighbour of the same depth or deeper)
+    same = [x for x in nbrs if depth[x] >= depth[v]]
+    if same:
+        p = parent.copy()
+        p[v] = same[0]
+        assert oracle.validate(adj, s, depth, p) == 7
+    # a two-cycle of parents
+    p = parent.copy()
+    a = v
+    b = int(parent[v])
+    p[b] = a
+    assert oracle.validate(adj, s, depth, p) in (6, 7)
+    # parent of an unreached vertex / reached vertex without parent
+    p = parent.copy()
+    p[v] = -1
+    assert oracle.validate(adj, s, depth, p) == 2
+    # wrong source entry
+    p = parent.copy()
+    p[s] = int(adj.col[adj.row_ptr[s]])
+    assert oracle.validate(adj, s, depth, p) == 1
+    # depth off by one on a vertex (edge gap > 1 or parent level breaks)
+    d = depth.copy()
+    d[v] += 2
+    assert oracle.validate(adj, s, d, parent) in (3, 7)
+    # a reached vertex marked unreached
+    d = depth.copy()
+    d[v] = -1
+    assert oracle.validate(adj, s, d, None) == 4
+    d = depth.copy()
+    d[v] = 0
+    assert oracle.validate(adj, s, d, None) == 8
+
+
+def test_level_stats_closed_form_path():
+    n = 9
+    adj = oracle.build_adjacency(n, np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32))
+    depth, _ = oracle.bfs(adj, 0)
+    st = oracle.level_stats(adj, depth)
+    deg = np.diff(adj.row_ptr)
+    assert st.shape == (n, 6)
+    for i in range(n):
+        f, e_f, u, s_u, d_new, e_u = st[i].tolist()
+        assert f == 1 and e_f == deg[i]
+        assert d_new == (1 if i < n - 1 else 0)
+        assert u == n - 1 - i
+        assert e_u == int(deg[i + 1:].sum())
+        assert s_u == (1 + e_u - deg[i + 1] if i < n - 1 else 0)
+
+
+def test_level_stats_closed_form_complete_graph_and_identities():
+    k = 10
+    pairs = np.array(list(itertools.combinations(range(k), 2)), np.int32)
+    adj = oracle.build_adjacency(k, pairs[:, 0], pairs[:, 1])
+    st = oracle.level_stats(adj, oracle.bfs(adj, 0)[0])
+    assert st.tolist() == [[1, k - 1, k - 1, k - 1, k - 1, (k - 1) ** 2],
+                           [k - 1, (k - 1) ** 2, 0, 0, 0, 0]]
+    n, src, dst = graphgen.rmat(11, 8, seed=31)
+    adj = oracle.build_adjacency(n, src, dst)
+    s = int(graphgen.sample_sources(n, src, dst, 1, seed=2)[0])
+    depth, _ = oracle.bfs(adj, s)
+    st = oracle.level_stats(adj, depth)
+    f, e_f, u, s_u, d_new, e_u = st.T
+    assert f.sum() == np.count_nonzero(depth >= 0)
+    assert np.array_equal(d_new[:-1], f[1:]) and d_new[-1] == 0
+    assert np.array_equal(u[:-1] - u[1:], d_new[:-1])   # P_{i+1} = P_i OR F_{i+1}
+    assert np.array_equal(e_u[:-1] - e_u[1:], e_f[1:])
+    assert np.all(s_u <= e_u) and np.all(s_u >= 0)
+
+
+def _random_params(seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, 0.4, oracle.mlp_num_params())
+
+
+def test_mlp_gradient_matches_central_finite_differences():
+    rng = np.random.default_rng(3)
+    P = _random_params(4)
+    X = rng.normal(0, 1, (17, oracle.N_IN))
+    y = rng.integers(0, oracle.N_OUT, 17).astype(np.int32)
+    loss, g = oracle.mlp_loss_grad(P, X, y)
+    h = 1e-6
+    num = np.empty_like(g)
+    for i in range(len(P)):
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        num[i] = (oracle.mlp_loss_grad(Pp, X, y)[0] - oracle.mlp_loss_grad(Pm, X, y)[0]) / (2 * h)
+    assert np.max(np.abs(num - g)) / np.max(np.abs(g)) < 1e-7
+    assert loss > 0
+
+
+def test_mlp_closed_forms():
+    P = np.zeros(oracle.mlp_num_params())
+    b3 = np.array([0.5, -1.0, 2.0])
+    P[-3:] = b3
+    X = np.random.default_rng(1).normal(0, 1, (5, oracle.N_IN))
+    assert np.allclose(oracle.mlp_forward(P, X), np.tile(b3, (5, 1)))
+    P[-3:] = 0
+    loss, g = oracle.mlp_loss_grad(P, X, np.array([0, 1, 2, 0, 1], np.int32))
+    assert abs(loss - np.log(3)) < 1e-15
+    # gradient wrt b3 is mean(softmax - onehot) = 1/3 - frequency of each class
+    assert np.allclose(g[-3:], np.array([1 / 3 - 2 / 5, 1 / 3 - 2 / 5, 1 / 3 - 1 / 5]))
+    # one hidden path: W1[0,0]=1, W2[0,0]=1, W3[j,0]=c_j gives z = c * relu(x0)
+    P = np.zeros(oracle.mlp_num_params())
+    P[0] = 1.0
+    off_w2 = 32 * 10 + 32
+    P[off_w2] = 1.0
+    off_w3 = off_w2 + 32 * 32 + 32
+    c = np.array([2.0, -3.0, 0.25])
+    P[off_w3 + 0] = c[0]; P[off_w3 + 32] = c[1]; P[off_w3 + 64] = c[2]
+    X = np.zeros((3, oracle.N_IN)); X[:, 0] = [1.5, -2.0, 0.0]
+    Z = oracle.mlp_forward(P, X)
+    assert np.allclose(Z, np.outer(np.maximum(X[:, 0], 0), c))
+
+
+def test_adam_first_step_is_lr_times_sign():
+    P = np.array([1.0, -2.0, 3.0]); m1 = np.zeros(3); m2 = np.zeros(3)
+    g = np.array([0.3, -5.0, 1e-3])
+    oracle.adam_step(P, m1, m2, g, t=1, lr=0.01, eps=1e-12)
+    assert np.allclose(P, [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01], atol=1e-9)
