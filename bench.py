@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark: direction-optimising BFS GTEPS on one GB300 (and N replicas).
+
+Workload (default): RMAT scale 22, edge factor 16, a=0.57 b=c=0.19 d=0.05,
+symmetrised, self-loops and duplicates removed, int32 CSR; 64 seeded sources
+of degree > 0 run one at a time with the plain push/pull direction switch.
+A step = the 64 searches.  value = undirected edges in the reached components
+summed over the sources / device time (GTEPS).  Also reported: the same 64
+sources as one 64-lane MS-BFS launch (batched) and with the learned policy,
+an end-to-end figure through the C ABI with host buffers, the roofline of the
+BFS kernel, and the CPU oracle on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat-s22-ef16")
+    ap.add_argument("--sources", type=int, default=64)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip batched / learned / ER extras")
+    ap.add_argument("--policy-weights", default=os.path.join(ROOT, "paper_2607_17106_gb300", "policy_weights.npy"))
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ roofline model
+def bytes_model(stats: np.ndarray, n: int):
+    """Minimum DRAM bytes of one search from its per-level statistics.
+
+    outputs: depth+parent written once per vertex (8n) and the visited bitmap
+    initialised once (n/8); per level the cheaper of
+      push: queue 4f + row offsets 8f + columns 4e_f + next queue 4d_new
+      pull: visited n/8 + row offsets 4u + scanned columns 4s_u + next bitmap n/8
+    """
+    f, e_f, u, s_u, d_new, e_u = (stats[:, i].astype(np.float64) for i in range(6))
+    push = 12 * f + 4 * e_f + 4 * d_new
+    pull = n / 8 + 4 * u + 4 * s_u + n / 8
+    return 8.0 * n + n / 8 + float(np.minimum(push, pull).sum())
+
+
+def teps_edges(stats: np.ndarray) -> float:
+    """Undirected edges with both ends reached = (sum of degrees over reached vertices) / 2."""
+    return float(stats[:, 1].sum()) / 2.0
+
+
+# ------------------------------------------------------------ clock sampling
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+                for nm, val in zip(names, s[4:8]):
+                    if val.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(n, src, dst, sources, budget_s=20.0, gpu_depth=None):
+    """The oracle as it stands, single-threaded, on a bounded sample of sources."""
+    import oracle
+    t0 = time.perf_counter()
+    adj = oracle.build_adjacency(n, src, dst)
+    build_s = time.perf_counter() - t0
+    edges = 0.0
+    t_bfs = 0.0
+    used = 0
+    parity = True
+    for j, s in enumerate(sources):
+        t1 = time.perf_counter()
+        depth, parent = oracle.bfs(adj, int(s))
+        t_bfs += time.perf_counter() - t1
+        deg = np.diff(adj.row_ptr)
+        edges += float(deg[depth >= 0].sum()) / 2.0
+        if gpu_depth is not None and j < len(gpu_depth):
+            parity = parity and bool(np.array_equal(depth, gpu_depth[j]))
+        used += 1
+        if t_bfs > budget_s:
+            break
+    return {"value": edges / t_bfs / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{used} of the workload's sources, FIFO queue BFS (adjacency build {build_s:.1f}s untimed)",
+            "parity_on_sample": parity}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    w = graphgen.WORKLOADS[args.workload]
+    n, src, dst = w.edges()
+    sources = w.sources(n, src, dst)
+    import oracle
+    adj = oracle.build_adjacency(n, src, dst)
+    deg = np.diff(adj.row_ptr)
+    times, edges = [], []
+    for step in range(args.warmup + args.steps):
+        s = int(sources[step % len(sources)])
+        t0 = time.perf_counter()
+        depth, _ = oracle.bfs(adj, s)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            edges.append(float(deg[depth >= 0].sum()) / 2.0)
+    value = sum(edges) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": "BFS GTEPS (plain direction-optimising, per source)", "value": value,
+            "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w.name, "sources": "one seeded source per step",
+                       "engine": "CPU oracle (FIFO queue BFS), single thread"},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single-source searches"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2607_17106_gb300 as bg
+    from paper_2607_17106_gb300 import build as bgbuild
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    bgbuild.build()
+    bg.load()
+    stream = torch.cuda.current_stream()
+
+    w = graphgen.WORKLOADS[args.workload]
+    n, src, dst = w.edges()
+    # weak scaling: every rank searches its own 64 seeded sources on a replica
+    sources = graphgen.sample_sources(n, src, dst, args.sources, w.source_seed + 1000 * rank)
+    g = bg.Graph.build(n, src, dst)
+    info = g.info()
+    k = len(sources)
+    depth = torch.empty((k, n), dtype=torch.int32, device="cuda")
+    parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
+    opt = bg.options(batch=0)
+
+    def plain_step(events=None):
+        for j in range(k):
+            if events is not None:
+                events[j][0].record(stream)
+            g.run(np.array([sources[j]], np.int32), depth[j], parent[j], opt)
+            if events is not None:
+                events[j][1].record(stream)
+
+    for _ in range(args.warmup):
+        plain_step()
+    g.sync()
+    torch.cuda.synchronize()
+
+    # per-source work (from the finished search) for TEPS and the roofline
+    depth_h = depth.cpu().numpy()
+    stats = [g.level_stats(depth[j]) for j in range(k)]
+    edges = sum(teps_edges(s) for s in stats)
+    bmin = [bytes_model(s, n) for s in stats]
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(k)]
+          for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        plain_step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    g.sync()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(args.steps) for j in range(k)]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * edges / (ms_per_step * 1e-3) / 1e9
+
+    peak, peak_kind = measured_peak()
+    mean_launch_s = float(np.mean(launch_ms)) * 1e-3
+    mean_bmin = float(np.mean(bmin))
+    achieved = mean_bmin / mean_launch_s / 1e9
+    roof = {"bound": "hbm", "kernel": "bfs1_kernel (persistent level loop)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS, "bytes_per_launch": mean_bmin,
+            "launch_us": mean_launch_s * 1e6, "traffic": None}
+
+    extra = {}
+    if not args.no_extra:
+        # batched: the same sources as one 64-lane MS-BFS launch
+        optb = bg.options(batch=1)
+        for _ in range(3):
+            g.run(sources, depth, parent, optb)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            g.run(sources, depth, parent, optb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g.sync()
+        bms = e0.elapsed_time(e1) / reps
+        same = bool(np.array_equal(depth.cpu().numpy(), depth_h))
+        extra["batched_msbfs"] = {"gteps": edges / (bms * 1e-3) / 1e9, "ms_per_step": bms,
+                                  "speedup_vs_plain": ms_per_step / bms, "depth_equal_to_plain": same}
+        if os.path.exists(args.policy_weights):
+            pol = bg.Policy(np.load(args.policy_weights))
+            optl = bg.options(batch=0, policy=bg.BFS_POLICY_MLP, mlp=pol)
+            for _ in range(2):
+                for j in range(k):
+                    g.run(np.array([sources[j]], np.int32), depth[j], parent[j], optl)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for j in range(k):
+                g.run(np.array([sources[j]], np.int32), depth[j], parent[j], optl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g.sync()
+            lms = e0.elapsed_time(e1)
+            extra["learned_single"] = {"gteps": edges / (lms * 1e-3) / 1e9, "ms_per_step": lms,
+                                       "speedup_vs_plain": ms_per_step / lms,
+                                       "depth_equal_to_plain": bool(np.array_equal(depth.cpu().numpy(), depth_h))}
+            optbl = bg.options(batch=1, policy=bg.BFS_POLICY_MLP, mlp=pol)
+            g.run(sources, depth, parent, optbl)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                g.run(sources, depth, parent, optbl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            blms = e0.elapsed_time(e1) / reps
+            extra["batched_learned"] = {"gteps": edges / (blms * 1e-3) / 1e9, "ms_per_step": blms,
+                                        "speedup_vs_plain": ms_per_step / blms}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()
+    depth_host = torch.empty((k, n), dtype=torch.int32).pin_memory()
+    parent_host = torch.empty((k, n), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.run(src_host, depth_host, parent_host, opt)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ws * edges / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
+           "d2h_bytes_per_step": 8 * k * n, "ms_per_step": e2e_s * 1e3,
+           "path": "bfs_run(k=64, host sources, host depth/parent, one source at a time)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, src, dst, sources[:8], budget_s=15.0, gpu_depth=depth_host.numpy()[:8])
+
+    if rank == 0:
+        line = {
+            "metric": "BFS GTEPS, plain single-source push/pull direction-optimising (batched+learned reported beside)",
+            "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{w.name}: RMAT scale 22, edge factor 16, a=0.57 b=c=0.19 d=0.05, "
+                                   f"symmetrised+dedup, n={n}, m={info.m} directed; {k} seeded sources "
+                                   f"one at a time", "sources_per_step": k, "edges_per_step": edges,
+                       "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
+                       "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=14 beta=24"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": k * args.steps,
+            "clocks": clk, **extra,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * bfs.h -- C ABI of the GB300-native breadth-first-search library (libbfsgb).
+ *
+ * The operation is level-synchronous BFS as written in the paper's Cascade 1
+ * ("The Einsum-Enabled Design Space for Graph Algorithms: A BFS Case Study",
+ * Section 3): every level is a masked Boolean sparse-matrix sparse-vector
+ * product F_{i+1} = (G x F_i) masked by NOT P_i (Eq. advance) followed by the
+ * visited-set update P_{i+1} = P_i OR F_{i+1} (Eq. update), stopping when the
+ * new frontier is empty.  A level runs either in push form (loop order s -> d,
+ * CSR expand of the frontier) or in pull form (loop order d -> s, Section 5:
+ * unvisited vertices scan their in-neighbours with early exit).
+ *
+ * Conventions for every call:
+ *   - The caller owns all input and output buffers.  A pointer may be host or
+ *     device memory; the library detects which (cudaPointerGetAttributes) and
+ *     copies through device staging buffers when needed.
+ *   - Work is ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls whose outputs are device memory return after enqueueing;
+ *     calls with host outputs synchronise the stream before returning.
+ *   - No exception crosses the ABI.  Every call returns a bfs_status; the
+ *     message of the last failure on the calling thread is bfs_last_error().
+ *   - A bfs_graph owns device memory and a per-graph workspace.  Runs on the
+ *     same graph must not overlap in time (use one stream per graph, or
+ *     synchronise between streams).
+ */
+#ifndef BFSGB_BFS_H
+#define BFSGB_BFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFS_OK = 0,
+    BFS_EINVAL = 1,    /* bad argument: null pointer, n <= 0, vertex id out of range, k <= 0 ... */
+    BFS_ENOMEM = 2,    /* device or host allocation failed */
+    BFS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    BFS_ETIMEOUT = 4,  /* a device-side wait (grid barrier) exceeded its limit; outputs undefined */
+    BFS_ERANGE = 5,    /* size beyond the int32 CSR limits (more than 2^31-1 directed entries) */
+    BFS_EVALIDATE = 6  /* internal consistency check failed (e.g. device error flag set) */
+} bfs_status;
+
+typedef struct bfs_graph bfs_graph;   /* opaque, library-owned */
+typedef struct bfs_policy bfs_policy; /* opaque, library-owned learned direction policy */
+
+/* Build flags for bfs_build_graph. */
+enum {
+    BFS_SYMMETRIZE = 1, /* add (d,s) for every (s,d): an undirected edge is two directed edges (Sec. 3) */
+    BFS_DEDUP = 2,      /* G is a 0/1 tensor (Eq. G): keep each (s,d) once */
+    BFS_DROP_SELF = 4,  /* drop s == d */
+    BFS_BUILD_CSC = 8,  /* build the d-major copy used by pull levels; aliases CSR when symmetric */
+    BFS_DEFAULT_FLAGS = 15
+};
+
+/*
+ * Build the graph tensor G (Cascade 1, Eq. G) in CSR form (Section 4.C) from an
+ * int32 edge list of m entries (src[e], dst[e]) over vertices [0, n).
+ * Rows are sorted ascending and, with BFS_DEDUP, free of repeats.  With
+ * BFS_BUILD_CSC the transpose (the rank swizzle of Section 4.B, B.4) is built
+ * for pull levels; when BFS_SYMMETRIZE is set it is the CSR itself.
+ * src/dst: host or device, not modified.  *out receives a new graph, freed
+ * with bfs_free_graph.  Errors: EINVAL (null pointer, n <= 0, m < 0, id
+ * outside [0, n)), ERANGE (more than 2^31-1 directed entries before or after
+ * deduplication), ENOMEM, ECUDA.  Synchronises `cuda_stream`.
+ */
+bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint32_t flags,
+                           void* cuda_stream, bfs_graph** out);
+
+/* Graph summary.  deg_* are out-degree statistics of the built CSR. */
+typedef struct {
+    int32_t n;
+    int64_t m;            /* directed CSR entries */
+    int32_t symmetric;    /* 1 when the CSC aliases the CSR */
+    int32_t n_isolated;   /* vertices of degree 0 */
+    int32_t deg_max;
+    double deg_mean;
+    double deg_var;       /* population variance of the out-degree */
+} bfs_graph_stats;
+
+bfs_status bfs_graph_info(const bfs_graph* g, bfs_graph_stats* out);
+
+/*
+ * Copy the CSR out: row_ptr[n+1] (int32) and col[m] (int32), host or device.
+ * With csc != 0 the d-major copy is copied instead.  Synchronises the stream
+ * when a destination is host memory.
+ */
+bfs_status bfs_graph_csr(const bfs_graph* g, int32_t csc, int32_t* row_ptr, int32_t* col, void* cuda_stream);
+
+void bfs_free_graph(bfs_graph* g);
+
+/* Traversal form of one level (the third class of the 3-way policy). */
+enum {
+    BFS_DIR_PUSH_QUEUE = 0,  /* push, sparse int32 queue frontier (GraphIt SparsePush) */
+    BFS_DIR_PUSH_BITMAP = 1, /* push, frontier read from the dense bitmap in vertex order (DensePush) */
+    BFS_DIR_PULL = 2         /* pull over unvisited vertices with early exit (DensePull, Section 5) */
+};
+
+/* How the level loop is driven. */
+enum {
+    BFS_MODE_PERSISTENT = 0, /* one cooperative kernel, levels separated by a grid barrier (default) */
+    BFS_MODE_HOST_LOOP = 1,  /* one launch sequence per level, 4-byte readback per level */
+    BFS_MODE_GRAPH = 2       /* CUDA graph with a conditional WHILE node: no host work per level */
+};
+
+/* Per-level direction policy. */
+enum {
+    BFS_POLICY_HEURISTIC = 0, /* Beamer: push->pull if e_f > m_u/alpha, pull->push if f < n/beta */
+    BFS_POLICY_PUSH = 1,      /* push every level (queue or bitmap by the gamma threshold) */
+    BFS_POLICY_PULL = 2,      /* pull every level */
+    BFS_POLICY_SCHEDULE = 3,  /* level i uses schedule[i % schedule_len] */
+    BFS_POLICY_MLP = 4        /* learned policy `mlp` (falls back to HEURISTIC when NULL) */
+};
+
+/* One record per executed level, written when bfs_options.level_log != NULL. */
+typedef struct {
+    int32_t level;
+    int32_t dir;          /* BFS_DIR_* used for this level */
+    int64_t f;            /* |F_i| */
+    int64_t e_f;          /* sum of degrees over F_i */
+    int64_t m_u;          /* sum of degrees over vertices unvisited before the level */
+    int64_t t_ns;         /* device %globaltimer at the start of the level */
+} bfs_level_record;
+
+typedef struct {
+    uint32_t struct_size;    /* sizeof(bfs_options); set by bfs_options_init */
+    int32_t mode;            /* BFS_MODE_* */
+    int32_t policy;          /* BFS_POLICY_* */
+    float alpha;             /* Beamer alpha (14) */
+    float beta;              /* Beamer beta (24) */
+    float gamma;             /* push levels read the bitmap when f > n / gamma (16) */
+    int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (2048) */
+    int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
+    int32_t pull_serial;     /* pull: entries one thread scans before a warp takes over (8) */
+    int32_t block_threads;   /* threads per CTA of the level kernels (512) */
+    int32_t blocks_per_sm;   /* CTAs per SM, 0 = as many as fit (persistent/cooperative launch) */
+    int32_t claim_aggregate; /* push: warp-aggregate the visited-bitmap OR by word (1) */
+    int64_t barrier_timeout_ns; /* limit of one device-side wait before BFS_ETIMEOUT (2e9) */
+    const int8_t* schedule;  /* host array for BFS_POLICY_SCHEDULE */
+    int32_t schedule_len;
+    int32_t max_levels;      /* stop with BFS_ERANGE after this many levels, 0 = n + 1 */
+    const bfs_policy* mlp;   /* for BFS_POLICY_MLP */
+    bfs_level_record* level_log; /* optional host array, one record per level (k = 1 only) */
+    int32_t level_log_cap;
+    int32_t* levels_out;     /* optional host int32: number of levels executed (k = 1: last run) */
+    int32_t batch;           /* k > 1: 1 = 64-lane MS-BFS batches (default), 0 = one source at a time */
+} bfs_options;
+
+/* Fill `opt` with the defaults listed above. */
+void bfs_options_init(bfs_options* opt);
+
+/*
+ * Breadth-first search from k sources (Cascade 1).  For every source j:
+ *   depth[j*n + v]  = hop distance from sources[j] to v, -1 if unreachable
+ *                     (the paper's empty value infinity, Eq. F)
+ *   parent[j*n + v] = a vertex u with (u, v) in G and depth u = depth v - 1
+ *                     (the ANY reduction of Eq. advance picks one; not unique),
+ *                     sources[j] for v = sources[j], -1 if unreachable.
+ * parent may be NULL.  Depths do not depend on the options; parents may.
+ * sources[k]: host or device.  depth/parent: [k][n] int32, host or device.
+ * k == 1 runs the single-source path; k > 1 runs 64-lane MS-BFS batches (or
+ * single sources when opt->batch == 0).
+ * Errors: EINVAL (null g/sources/depth, k <= 0, source outside [0, n)),
+ * ENOMEM, ECUDA, ETIMEOUT (outputs undefined), ERANGE (max_levels exceeded).
+ */
+bfs_status bfs_run(const bfs_graph* g, const int32_t* sources, int32_t k, int32_t* depth, int32_t* parent,
+                   const bfs_options* opt, void* cuda_stream);
+
+/*
+ * Wait for `cuda_stream` and report the first device-side failure (barrier
+ * timeout, work-list overflow, level limit) raised by any asynchronous run on
+ * `g` since the previous check; the failure is cleared once reported.
+ */
+bfs_status bfs_sync(const bfs_graph* g, void* cuda_stream);
+
+/*
+ * Many queries over several graphs in ONE persistent launch: query q searches
+ * graphs[graph_of_query[q]] from sources[q]; its outputs go to depth[q] and
+ * parent[q] (each an int32 array of that graph's n; device memory).
+ * graph_of_query/sources are host arrays of length nq; graphs has n_graphs
+ * entries; depth/parent are host arrays of nq device pointers (parent or its
+ * entries may be NULL).  Queries are grouped per graph into 64-lane units and
+ * the units are handed out to CTA teams by a device work counter.
+ * Errors as bfs_run.
+ */
+bfs_status bfs_run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
+                         const int32_t* sources, int32_t nq, int32_t* const* depth, int32_t* const* parent,
+                         const bfs_options* opt, void* cuda_stream);
+
+/*
+ * Per-level work statistics of a finished search, for the roofline model:
+ * for levels i = 0 .. L-1 six int64 values [f, e_f, u, s_u, d_new, e_u]:
+ * |F_i|, degree sum over F_i, non-isolated vertices unvisited before level i,
+ * CSR entries a pull level reads (each unvisited row scanned in ascending
+ * order up to its first neighbour of depth i, or fully; Section 5), |F_{i+1}|
+ * and the degree sum over the unvisited vertices.  depth[n]: host or device
+ * output of bfs_run for one source.  stats: host array of 6*max_levels int64.
+ * *levels receives L.  Errors: EINVAL, ERANGE (L > max_levels).  Synchronises.
+ */
+bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
+                           int32_t* levels, void* cuda_stream);
+
+/* ----------------------------------------------------- learned policy (MLP) */
+/*
+ * Direction policy: an FP32 MLP 10 -> 32 -> 32 -> 3 (ReLU) whose argmax picks
+ * BFS_DIR_*.  The paper has no learned policy; it replaces the Beamer switch
+ * it cites (Section 5).  Parameter layout (1507 floats, row-major):
+ *   W1[32][10] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]
+ * followed by 20 floats of input normalisation: mean[10], inv_std[10].
+ */
+#define BFS_MLP_IN 10
+#define BFS_MLP_HIDDEN 32
+#define BFS_MLP_OUT 3
+#define BFS_MLP_NPARAM 1507
+#define BFS_MLP_NNORM 20
+
+/* Features of one level (host or device float[10]) from its counters. */
+bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,
+                               int32_t prev_dir, float* out10);
+
+/* weights: host float[nw], nw = BFS_MLP_NPARAM + BFS_MLP_NNORM. */
+bfs_status bfs_policy_load(const float* weights, int32_t nw, bfs_policy** out);
+bfs_status bfs_policy_weights(const bfs_policy* p, float* out, int32_t nw); /* host copy */
+void bfs_policy_free(bfs_policy* p);
+
+/* logits[rows][3] for raw (unnormalised) features X[rows][10]; device pointers. */
+bfs_status bfs_policy_forward(const bfs_policy* p, const float* X, int64_t rows, float* logits,
+                              void* cuda_stream);
+
+/*
+ * One optimiser step of mean softmax cross-entropy on (X[rows][10], y[rows])
+ * with Adam (Kingma & Ba 2015): forward, backward and update run in the
+ * library's FP32 kernels on the device.  X/y: device.  loss_out: host float or
+ * NULL.  grad_out: optional device float[BFS_MLP_NPARAM] receiving the
+ * gradient before the update.  step is 1-based.
+ */
+bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const int32_t* y, int64_t rows, float lr,
+                                 int32_t step, float* loss_out, float* grad_out, void* cuda_stream);
+
+/* Replace the normalisation (mean[10], inv_std[10], host) used by forward/train. */
+bfs_status bfs_policy_set_norm(bfs_policy* p, const float* mean_inv_std);
+
+/* ------------------------------------------------------------------ errors */
+const char* bfs_status_string(bfs_status s);
+const char* bfs_last_error(void); /* thread-local message of the last failure */
+const char* bfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFSGB_BFS_H */

@@ -289,7 +289,7 @@ int or_validate(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t s
 /* ------------------------------------------------------------- MLP (FP64) */
 /*
  * Parameter vector layout (float64 here, float32 on the device), row-major:
- *   W1[32][10], b1[32], W2[32][32], b2[32], W3[3][32], b3[3]   (1491 values)
+ *   W1[32][10], b1[32], W2[32][32], b2[32], W3[3][32], b3[3]   (1507 values)
  * Forward: h1 = relu(W1 x + b1); h2 = relu(W2 h1 + b2); z = W3 h2 + b3.
  */
 enum { OR_IN = 10, OR_H = 32, OR_OUT = 3 };

@@ -1,0 +1,210 @@
+// capi.cu -- C ABI entry points: options, bfs_run dispatch, error reporting.
+#include "common.cuh"
+
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+namespace bfsgb {
+
+static thread_local std::string t_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+}
+
+bfs_status fail(bfs_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return s;
+}
+
+bfs_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    cudaGetLastError();  // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? BFS_ENOMEM : BFS_ECUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int device_id() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int d = device_id();
+    if (d < 0 || d >= 64) d = 0;
+    if (!cached[d]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        cached[d] = v > 0 ? v : 1;
+    }
+    return cached[d];
+}
+
+bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* parent, const bfs_options& o,
+                      const float* mlp_dev, cudaStream_t st);
+bfs_status run_msbfs(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* depth, int32_t* parent,
+                     const bfs_options& o, const float* mlp_dev, cudaStream_t st);
+bfs_status run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
+                     const int32_t* sources, int32_t nq, int32_t* const* depth, int32_t* const* parent,
+                     const bfs_options& o, cudaStream_t st);
+bfs_status sync_graph(bfs_graph* g, cudaStream_t st);
+const float* policy_device_weights(const bfs_policy* p);
+
+}  // namespace bfsgb
+
+using namespace bfsgb;
+
+extern "C" void bfs_options_init(bfs_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->struct_size = sizeof(bfs_options);
+    o->mode = BFS_MODE_PERSISTENT;
+    o->policy = BFS_POLICY_HEURISTIC;
+    o->alpha = 14.0f;
+    o->beta = 24.0f;
+    o->gamma = 16.0f;
+    o->chunk = 2048;
+    o->medium = 32;
+    o->pull_serial = 8;
+    o->block_threads = 512;
+    o->blocks_per_sm = 0;
+    o->claim_aggregate = 1;
+    o->barrier_timeout_ns = 2000000000ll;
+    o->batch = 1;
+}
+
+static bfs_status check_options(const bfs_options* in, bfs_options* o) {
+    bfs_options_init(o);
+    if (!in) return BFS_OK;
+    if (in->struct_size != sizeof(bfs_options)) return fail(BFS_EINVAL, "bfs_options.struct_size mismatch (call bfs_options_init)");
+    *o = *in;
+    if (o->mode < 0 || o->mode > 2) return fail(BFS_EINVAL, "bad mode %d", o->mode);
+    if (o->policy < 0 || o->policy > 4) return fail(BFS_EINVAL, "bad policy %d", o->policy);
+    if (o->chunk < 64) return fail(BFS_EINVAL, "chunk must be >= 64");
+    if (o->medium < 1) return fail(BFS_EINVAL, "medium must be >= 1");
+    if (o->pull_serial < 0) return fail(BFS_EINVAL, "pull_serial must be >= 0");
+    if (!(o->alpha > 0) || !(o->beta > 0) || !(o->gamma > 0)) return fail(BFS_EINVAL, "alpha, beta, gamma must be > 0");
+    if (o->barrier_timeout_ns <= 0) return fail(BFS_EINVAL, "barrier_timeout_ns must be > 0");
+    if (o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
+        return fail(BFS_EINVAL, "block_threads must be 256, 512 or 1024");
+    return BFS_OK;
+}
+
+extern "C" bfs_status bfs_run(const bfs_graph* gc, const int32_t* sources, int32_t k, int32_t* depth, int32_t* parent,
+                              const bfs_options* opt, void* cuda_stream) {
+    bfs_graph* g = const_cast<bfs_graph*>(gc);
+    if (!g) return fail(BFS_EINVAL, "graph is NULL");
+    if (!sources || !depth) return fail(BFS_EINVAL, "sources/depth is NULL");
+    if (k <= 0) return fail(BFS_EINVAL, "k must be positive (got %d)", k);
+    bfs_options o;
+    bfs_status s = check_options(opt, &o);
+    if (s != BFS_OK) return s;
+    if (device_id() != g->device) return fail(BFS_EINVAL, "graph lives on device %d, current device is %d", g->device, device_id());
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<int32_t> src(k);
+    if (is_device_ptr(sources)) {
+        BFS_CUDA(cudaMemcpyAsync(src.data(), sources, (size_t)k * 4, cudaMemcpyDeviceToHost, st));
+        BFS_CUDA(cudaStreamSynchronize(st));
+    } else {
+        memcpy(src.data(), sources, (size_t)k * 4);
+    }
+    for (int j = 0; j < k; ++j)
+        if (src[j] < 0 || src[j] >= g->n) return fail(BFS_EINVAL, "source %d = %d outside [0, %d)", j, src[j], g->n);
+    const float* mlp = (o.policy == BFS_POLICY_MLP) ? policy_device_weights(o.mlp) : nullptr;
+    std::lock_guard<std::mutex> lk(g->lock);
+    bool dev_out = is_device_ptr(depth) && (!parent || is_device_ptr(parent));
+    if (k > 1 && o.batch) {
+        return run_msbfs(g, src.data(), k, depth, parent, o, mlp, st);
+    }
+    const int64_t n = g->n;
+    if (dev_out) {
+        for (int j = 0; j < k; ++j) {
+            s = run_single(g, src[j], depth + j * n, parent ? parent + j * n : nullptr, o, mlp, st);
+            if (s != BFS_OK) return s;
+        }
+        return BFS_OK;
+    }
+    // host outputs: stage through device buffers
+    int32_t *dd = nullptr, *dp = nullptr;
+    if (cudaMallocAsync(&dd, n * 4, st) != cudaSuccess || (parent && cudaMallocAsync(&dp, n * 4, st) != cudaSuccess)) {
+        cudaGetLastError();
+        if (dd) cudaFreeAsync(dd, st);
+        return fail(BFS_ENOMEM, "staging buffers");
+    }
+    for (int j = 0; j < k && s == BFS_OK; ++j) {
+        s = run_single(g, src[j], dd, dp, o, mlp, st);
+        if (s != BFS_OK) break;
+        cudaError_t e = cudaMemcpyAsync(depth + j * n, dd, n * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent + j * n, dp, n * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "copy outputs to host");
+    }
+    cudaFreeAsync(dd, st);
+    if (dp) cudaFreeAsync(dp, st);
+    if (s == BFS_OK) s = sync_graph(g, st);
+    return s;
+}
+
+extern "C" bfs_status bfs_run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
+                                    const int32_t* sources, int32_t nq, int32_t* const* depth, int32_t* const* parent,
+                                    const bfs_options* opt, void* cuda_stream) {
+    if (!graphs || n_graphs <= 0 || !graph_of_query || !sources || nq <= 0 || !depth)
+        return fail(BFS_EINVAL, "null argument or empty batch");
+    bfs_options o;
+    bfs_status s = check_options(opt, &o);
+    if (s != BFS_OK) return s;
+    for (int g = 0; g < n_graphs; ++g)
+        if (!graphs[g]) return fail(BFS_EINVAL, "graphs[%d] is NULL", g);
+    for (int q = 0; q < nq; ++q) {
+        int gi = graph_of_query[q];
+        if (gi < 0 || gi >= n_graphs) return fail(BFS_EINVAL, "graph_of_query[%d] = %d", q, gi);
+        if (sources[q] < 0 || sources[q] >= graphs[gi]->n) return fail(BFS_EINVAL, "sources[%d] out of range", q);
+        if (!depth[q] || !is_device_ptr(depth[q])) return fail(BFS_EINVAL, "depth[%d] must be device memory", q);
+        if (parent && parent[q] && !is_device_ptr(parent[q])) return fail(BFS_EINVAL, "parent[%d] must be device memory", q);
+    }
+    return run_mixed(graphs, n_graphs, graph_of_query, sources, nq, depth, parent, o, (cudaStream_t)cuda_stream);
+}
+
+extern "C" bfs_status bfs_sync(const bfs_graph* g, void* cuda_stream) {
+    if (!g) return fail(BFS_EINVAL, "graph is NULL");
+    return sync_graph(const_cast<bfs_graph*>(g), (cudaStream_t)cuda_stream);
+}
+
+extern "C" const char* bfs_status_string(bfs_status s) {
+    switch (s) {
+        case BFS_OK: return "ok";
+        case BFS_EINVAL: return "invalid argument";
+        case BFS_ENOMEM: return "out of memory";
+        case BFS_ECUDA: return "CUDA error";
+        case BFS_ETIMEOUT: return "device wait timed out";
+        case BFS_ERANGE: return "size out of range";
+        case BFS_EVALIDATE: return "consistency check failed";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* bfs_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" const char* bfs_version(void) { return "bfsgb 0.1 (sm_103a)"; }

@@ -1,0 +1,179 @@
+// common.cuh -- internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <mutex>
+
+#include "../../include/bfs.h"
+
+namespace bfsgb {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+bfs_status fail(bfs_status s, const char* fmt, ...);
+bfs_status cuda_fail(cudaError_t e, const char* what);
+
+#define BFS_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::bfsgb::cuda_fail(_e, #call); \
+    } while (0)
+
+// Pointer classification: true when p is device-accessible memory on the
+// current device (device or managed); false for pageable or pinned host.
+bool is_device_ptr(const void* p);
+
+// ------------------------------------------------------ device error codes
+enum : int32_t {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,     // a grid/team barrier wait exceeded its limit
+    DEV_OVERFLOW = 2,    // a work list exceeded its capacity
+    DEV_LEVELS = 3       // max_levels exceeded
+};
+
+// ------------------------------------------------------------------ graph
+struct Workspace1;   // single-source state (bfs_single.cu)
+struct WorkspaceMS;  // MS-BFS state (msbfs.cu)
+
+}  // namespace bfsgb
+
+struct bfs_graph {
+    int32_t n = 0;
+    int64_t m = 0;            // directed CSR entries
+    int32_t symmetric = 0;
+    int32_t device = 0;
+    int32_t* row_ptr = nullptr;   // [n+1]
+    int32_t* col = nullptr;       // [m]
+    int32_t* csc_ptr = nullptr;   // [n+1], == row_ptr when symmetric
+    int32_t* csc_col = nullptr;   // [m],   == col when symmetric
+    uint32_t* isolated = nullptr; // [W] bit v set iff deg(v) == 0 (out- and in-degree)
+    int32_t n_isolated = 0;
+    int32_t deg_max = 0;
+    double deg_mean = 0, deg_var = 0;
+    int64_t n_big_units = 0;      // sizing of push chunk units, per chunk size (set on first run)
+    std::mutex lock;
+    bfsgb::Workspace1* ws1 = nullptr;
+    bfsgb::WorkspaceMS* wsms = nullptr;
+};
+
+namespace bfsgb {
+
+void free_ws1(Workspace1*);
+void free_wsms(WorkspaceMS*);
+
+__host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------ device primitives
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
+
+// Grid barrier state: one per persistent launch (zeroed before launch).
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int abort;    // set by any CTA that gives up; every waiter checks it
+    int err;      // DEV_* code of the first failure
+};
+
+// Barrier over `nblocks` co-resident CTAs (cooperative launch).  Spins on the
+// generation word with a %globaltimer limit; on expiry it records DEV_TIMEOUT,
+// raises the abort flag and returns false, so every CTA leaves its loop.
+// Returns false when the barrier was aborted (by this CTA or another).
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, int64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(&b->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&b->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            st_release_u32(&b->gen, gen + 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(&b->gen) == gen) {
+                if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
+                if ((++spins & 63u) == 1 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) {
+                    atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);
+                    atomicExch(&b->abort, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ld_volatile_i32(&b->abort)) ok = 0;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
+// Returns the exclusive prefix; *total receives the block sum.  Uses `tmp`
+// (>= 33 ints of shared memory).
+__device__ __forceinline__ int block_exclusive_scan(int x, int* tmp, int* total) {
+    unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned nw = (blockDim.x + 31) >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < nw) ? tmp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if ((int)lane >= o) wi += y;
+        }
+        if (lane < nw) tmp[lane] = wi - w;
+        if (lane == 31) tmp[32] = wi;
+    }
+    __syncthreads();
+    int r = tmp[warp] + incl - x;
+    *total = tmp[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ------------------------------------------------------------- launching
+int num_sms();
+int device_id();
+
+}  // namespace bfsgb

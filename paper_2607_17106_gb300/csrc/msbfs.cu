@@ -1,0 +1,783 @@
+// msbfs.cu -- batched multi-source BFS: up to 64 sources per unit, each
+// vertex carrying 64-bit frontier / seen masks (one bit per source lane).
+//
+// Per lane j this is exactly Cascade 1 for source j; the 64 lanes share every
+// read of G.  With seen_i the lanes that reached v before level i and front_i
+// the lanes whose frontier holds v:
+//   push: for u with front_i[u] != 0, for v in N(u):
+//           new = front_i[u] & ~seen[v]; atomicOr(next[v], new)
+//   pull: for v with missing = ~seen[v] != 0, OR front_i[u] over in-neighbours
+//           u in ascending order, stopping once every missing lane is found
+//   then front_{i+1} = next and seen |= next: the three-array identity
+//   F_{i+1} = P_{i+1} AND NOT P_i of the paper's variant 26.
+// The ANY reduction picks, per lane, the first u (push: the one whose OR set
+// the bit; pull: the lowest-index in-neighbour), which is written as parent.
+//
+// One cooperative kernel runs all levels of all units of a launch: units are
+// independent searches (possibly over different graphs: bfs_run_mixed), and
+// levels are separated by a grid barrier with a %globaltimer limit.
+#include "common.cuh"
+#include "policy_dev.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+namespace bfsgb {
+
+struct MsUnit {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const int32_t* csc_ptr;
+    const int32_t* csc_col;
+    const uint32_t* isolated;
+    int64_t m;
+    int32_t n;
+    int32_t k;
+    int32_t symmetric;
+    int32_t deg_max;
+    int32_t src[64];
+    int32_t* depth[64];
+    int32_t* parent[64];
+};
+
+struct CountersMS {
+    unsigned long long a_len;  // active vertices appended (front != 0)
+    unsigned long long u_len;  // chunk units appended
+    unsigned long long e_f;    // degree sum of the appended vertices
+    unsigned long long work;   // work counter of the level that fills this slot
+};
+
+struct CtlMS {
+    GridBarrier bar;
+    CountersMS slot[3];
+    int32_t levels;
+};
+
+struct WorkspaceMS {
+    int32_t ncap = 0;
+    int64_t ucap = 0;
+    int32_t chunk = 0;
+    uint64_t* seen = nullptr;
+    uint64_t* front[2] = {nullptr, nullptr};
+    int32_t* act[2] = {nullptr, nullptr};
+    int2* U[2] = {nullptr, nullptr};
+    CtlMS* ctl = nullptr;
+    int* d_sticky = nullptr;
+    MsUnit* d_units = nullptr;
+    int32_t units_cap = 0;
+    CtlMS* h_ctl = nullptr;
+};
+
+void free_wsms(WorkspaceMS* w) {
+    if (!w) return;
+    cudaFree(w->seen);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(w->front[i]);
+        cudaFree(w->act[i]);
+        cudaFree(w->U[i]);
+    }
+    cudaFree(w->ctl);
+    cudaFree(w->d_sticky);
+    cudaFree(w->d_units);
+    cudaFreeHost(w->h_ctl);
+    delete w;
+}
+
+int msbfs_sticky_error(bfs_graph* g) {
+    if (!g || !g->wsms) return 0;
+    int err = 0;
+    if (cudaMemcpy(&err, g->wsms->d_sticky, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return DEV_OK;
+    if (err) cudaMemset(g->wsms->d_sticky, 0, 4);
+    return err;
+}
+
+bfs_status device_error(int err, int64_t timeout_ns);
+const float* policy_device_weights(const bfs_policy* p);
+
+struct ParamsMS {
+    const MsUnit* units;
+    int32_t n_units;
+    uint64_t* seen;
+    uint64_t* F0;
+    uint64_t* F1;
+    int32_t* A0;
+    int32_t* A1;
+    int2* U0;
+    int2* U1;
+    int64_t ucap;
+    CtlMS* ctl;
+    int* sticky;
+    int32_t policy;
+    float alpha, beta;
+    const int8_t* schedule;
+    int32_t schedule_len;
+    const float* mlp;
+    int32_t chunk, medium, pull_serial;
+    int64_t timeout_ns;
+    int32_t max_levels;
+};
+
+// Unit fields kept in registers / shared memory while a unit runs.
+struct UnitView {
+    const int32_t* __restrict__ row_ptr;
+    const int32_t* __restrict__ col;
+    const int32_t* __restrict__ csc_ptr;
+    const int32_t* __restrict__ csc_col;
+    const uint32_t* __restrict__ isolated;
+    int64_t m;
+    int32_t n;
+    int32_t k;
+    int32_t symmetric;
+    uint64_t lanes;
+};
+
+struct MsSmem {
+    int32_t* depth[64];
+    int32_t* parent[64];
+    int off[513];
+    int beg[512];
+    int src[512];
+    unsigned long long fmask[512];
+    int scan_tmp[33];
+    int item;
+    float feat[BFS_MLP_IN];
+    float mlp_out;
+    unsigned long long red[16];
+};
+
+struct MsLevel {
+    int32_t level;
+    uint64_t* f_next;
+    int32_t* a_next;
+    int2* u_next;
+    CountersMS* next;
+    unsigned long long ef;
+};
+
+__device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, int par, int d) {
+    while (bits) {
+        int j = __ffsll((long long)bits) - 1;
+        sm.depth[j][v] = d;
+        if (sm.parent[j]) sm.parent[j][v] = par;
+        bits &= bits - 1;
+    }
+}
+
+// v became active in F_{i+1} (first touch): append to the active list,
+// degree sum, chunk units for big rows.  Warp-uniform.
+__device__ __forceinline__ void ms_emit(const ParamsMS& p, const UnitView& g, MsLevel& L, bool first, int v, int deg) {
+    unsigned cm = __ballot_sync(0xffffffffu, first);
+    if (!cm) return;
+    int leader = __ffs(cm) - 1;
+    unsigned long long base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(&L.next->a_len, (unsigned long long)__popc(cm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (first) {
+        L.a_next[base + __popc(cm & lanemask_lt())] = v;
+        L.ef += (unsigned long long)deg;
+        if (deg >= p.chunk) {
+            int nch = (deg + p.chunk - 1) / p.chunk;
+            unsigned long long ub = atomicAdd(&L.next->u_len, (unsigned long long)nch);
+            if (ub + nch <= (unsigned long long)p.ucap) {
+                for (int c = 0; c < nch; ++c) L.u_next[ub + c] = make_int2(v, c);
+            } else {
+                atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void ms_candidate(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, bool has,
+                                             int v, int u, uint64_t fu) {
+    uint64_t bits = 0;
+    if (has) bits = fu & ~__ldcg((const unsigned long long*)p.seen + v);
+    bool first = false;
+    int deg = 0;
+    if (bits) {
+        uint64_t old = atomicOr((unsigned long long*)L.f_next + v, (unsigned long long)bits);
+        uint64_t nb = bits & ~old;
+        first = (old == 0);
+        if (nb) write_lanes(sm, nb, v, u, L.level + 1);
+        if (first) deg = __ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v);
+    }
+    ms_emit(p, g, L, first, v, deg);
+}
+
+template <int T>
+__device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, int u) {
+    unsigned lane = lane_id();
+    int beg = 0, end = 0;
+    uint64_t fu = 0;
+    if (u >= 0) {
+        beg = __ldg(g.row_ptr + u);
+        end = __ldg(g.row_ptr + u + 1);
+        fu = __ldcg((const unsigned long long*)(((L.level & 1) ? p.F1 : p.F0)) + u);
+        if (end - beg >= p.chunk) end = beg;
+    }
+    bool med = (end - beg) >= p.medium;
+    unsigned mm = __ballot_sync(0xffffffffu, med);
+    while (mm) {
+        int l = __ffs(mm) - 1;
+        int ub = __shfl_sync(0xffffffffu, u, l);
+        int bb = __shfl_sync(0xffffffffu, beg, l);
+        int ee = __shfl_sync(0xffffffffu, end, l);
+        uint64_t fl = __shfl_sync(0xffffffffu, (unsigned long long)fu, l);
+        for (int base = bb; base < ee; base += 32) {
+            int j = base + (int)lane;
+            bool has = j < ee;
+            int v = has ? __ldg(g.col + j) : 0;
+            ms_candidate(p, g, L, sm, has, v, ub, fl);
+        }
+        mm &= mm - 1;
+    }
+    if (med) end = beg;
+    int deg = end - beg, total;
+    int off = block_exclusive_scan(deg, sm.scan_tmp, &total);
+    sm.off[threadIdx.x] = off;
+    sm.beg[threadIdx.x] = beg;
+    sm.src[threadIdx.x] = u;
+    sm.fmask[threadIdx.x] = fu;
+    if (threadIdx.x == T - 1) sm.off[T] = total;
+    __syncthreads();
+    for (int k0 = 0; k0 < total; k0 += T) {
+        int k = k0 + threadIdx.x;
+        bool has = k < total;
+        int v = 0, su = 0;
+        uint64_t sf = 0;
+        if (has) {
+            int lo = 0, hi = T - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (sm.off[mid] <= k) lo = mid; else hi = mid - 1;
+            }
+            su = sm.src[lo];
+            sf = sm.fmask[lo];
+            v = __ldg(g.col + sm.beg[lo] + (k - sm.off[lo]));
+        }
+        ms_candidate(p, g, L, sm, has, v, su, sf);
+    }
+    __syncthreads();
+}
+
+template <int T>
+__device__ void ms_push_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const int32_t* a_cur,
+                              const int2* u_cur, const uint64_t* f_cur, long long a, long long nunits, CountersMS* work) {
+    long long ntiles = (a + T - 1) / T;
+    long long nitems = nunits + ntiles;
+    while (true) {
+        if (threadIdx.x == 0) sm.item = (int)atomicAdd(&work->work, 1ull);
+        __syncthreads();
+        long long it = sm.item;
+        __syncthreads();
+        if (it >= nitems) break;
+        if (it < nunits) {
+            int2 un = __ldcg(u_cur + it);
+            int u = un.x;
+            uint64_t fu = __ldcg((const unsigned long long*)f_cur + u);
+            int b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
+            int lo = b + un.y * p.chunk, hi = min(e, lo + p.chunk);
+            for (int base = lo; base < hi; base += T) {
+                int j = base + threadIdx.x;
+                bool has = j < hi;
+                int v = has ? __ldg(g.col + j) : 0;
+                ms_candidate(p, g, L, sm, has, v, u, fu);
+            }
+        } else {
+            long long q = (it - nunits) * T + threadIdx.x;
+            int u = q < a ? __ldcg(a_cur + q) : -1;
+            ms_push_tile<T>(p, g, L, sm, u);
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
+    unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
+    unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(x >> 32));
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const uint64_t* f_cur) {
+    unsigned lane = lane_id();
+    long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int dnext = L.level + 1;
+    for (long long base = gwarp * 32; base < g.n; base += nwarps * 32) {
+        long long v = base + lane;
+        uint64_t miss = 0;
+        if (v < g.n) {
+            bool iso = (__ldg(g.isolated + (v >> 5)) >> (v & 31)) & 1u;
+            if (!iso) miss = g.lanes & ~__ldcg((const unsigned long long*)p.seen + v);
+        }
+        if (!__ballot_sync(0xffffffffu, miss != 0)) continue;
+        int beg = 0, end = 0;
+        if (miss) {
+            beg = __ldg(g.csc_ptr + v);
+            end = __ldg(g.csc_ptr + v + 1);
+        }
+        uint64_t acc = 0;
+        int j = beg;
+        int lim = min(end, beg + p.pull_serial);
+        for (; j < lim && acc != miss; ++j) {
+            int u = __ldg(g.csc_col + j);
+            uint64_t got = __ldcg((const unsigned long long*)f_cur + u) & miss & ~acc;
+            if (got) {
+                acc |= got;
+                write_lanes(sm, got, (int)v, u, dnext);
+            }
+        }
+        unsigned rm = __ballot_sync(0xffffffffu, miss != 0 && acc != miss && j < end);
+        while (rm) {
+            int l = __ffs(rm) - 1;
+            int jl = __shfl_sync(0xffffffffu, j, l);
+            int el = __shfl_sync(0xffffffffu, end, l);
+            uint64_t ml = __shfl_sync(0xffffffffu, (unsigned long long)miss, l);
+            uint64_t al = __shfl_sync(0xffffffffu, (unsigned long long)acc, l);
+            int vl = (int)(base + l);
+            for (int b2 = jl; b2 < el && al != ml; b2 += 32) {
+                int idx = b2 + (int)lane;
+                int uu = 0;
+                uint64_t fu = 0;
+                if (idx < el) {
+                    uu = __ldg(g.csc_col + idx);
+                    fu = __ldcg((const unsigned long long*)f_cur + uu) & ml & ~al;
+                }
+                uint64_t got = warp_or64(fu);
+                uint64_t gb = got;
+                while (gb) {  // warp-uniform: the first (lowest index) provider of each lane
+                    int bj = __ffsll((long long)gb) - 1;
+                    unsigned who = __ballot_sync(0xffffffffu, (fu >> bj) & 1ull);
+                    int par = __shfl_sync(0xffffffffu, uu, __ffs(who) - 1);
+                    if (lane == 0) {
+                        sm.depth[bj][vl] = dnext;
+                        if (sm.parent[bj]) sm.parent[bj][vl] = par;
+                    }
+                    gb &= gb - 1;
+                }
+                al |= got;
+            }
+            if ((int)lane == l) acc = al;
+            rm &= rm - 1;
+        }
+        bool first = acc != 0;
+        int deg = 0;
+        if (first) {
+            ((unsigned long long*)L.f_next)[v] = acc;
+            ((unsigned long long*)p.seen)[v] |= acc;
+            deg = g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
+        }
+        ms_emit(p, g, L, first, (int)v, deg);
+    }
+}
+
+__device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int level, long long a, long long e_f,
+                         long long m_u, long long a_prev, int prev_dir, int deg_max) {
+    int d;
+    switch (p.policy) {
+        case BFS_POLICY_PUSH: return BFS_DIR_PUSH_QUEUE;
+        case BFS_POLICY_PULL: return BFS_DIR_PULL;
+        case BFS_POLICY_SCHEDULE:
+            d = p.schedule[level % p.schedule_len];
+            return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
+        case BFS_POLICY_MLP:
+            if (p.mlp) {
+                if (threadIdx.x < 32) {
+                    if (threadIdx.x == 0)
+                        policy_features(sm.feat, a, e_f, m_u, level, prev_dir, g.n, log2f((float)g.n),
+                                        log2f(1.0f + (float)g.m), log2f(1.0f + (float)deg_max));
+                    __syncwarp();
+                    int c = policy_argmax_warp(p.mlp, sm.feat);
+                    if (threadIdx.x == 0) sm.mlp_out = (float)c;
+                }
+                __syncthreads();
+                d = (int)sm.mlp_out;
+                __syncthreads();
+                return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
+            }
+            // no weights: fall through to the heuristic
+        default:
+            if (prev_dir == BFS_DIR_PULL) {
+                bool stay = (a >= a_prev) || ((double)a * p.beta > (double)g.n);
+                return stay ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
+            }
+            if ((double)e_f * p.alpha > (double)m_u && a > a_prev) return BFS_DIR_PULL;
+            return BFS_DIR_PUSH_QUEUE;
+    }
+}
+
+template <int T>
+__device__ void msbfs_body(const ParamsMS& p) {
+    __shared__ MsSmem sm;
+    CtlMS* ctl = p.ctl;
+    const unsigned nblocks = gridDim.x;
+    const long long gtid = (long long)blockIdx.x * T + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * T;
+    int total_levels = 0;
+    for (int ui = 0; ui < p.n_units; ++ui) {
+        const MsUnit* U = p.units + ui;
+        UnitView g;
+        g.row_ptr = U->row_ptr;
+        g.col = U->col;
+        g.csc_ptr = U->csc_ptr;
+        g.csc_col = U->csc_col;
+        g.isolated = U->isolated;
+        g.m = U->m;
+        g.n = U->n;
+        g.k = U->k;
+        g.symmetric = U->symmetric;
+        g.lanes = (g.k >= 64) ? ~0ull : ((1ull << g.k) - 1);
+        int deg_max = U->deg_max;
+        if (threadIdx.x < 64) {
+            sm.depth[threadIdx.x] = threadIdx.x < g.k ? U->depth[threadIdx.x] : nullptr;
+            sm.parent[threadIdx.x] = threadIdx.x < g.k ? U->parent[threadIdx.x] : nullptr;
+        }
+        __syncthreads();
+        // init: masks, outputs (-1), counters
+        for (long long v = gtid; v < g.n; v += gthreads) {
+            p.seen[v] = 0;
+            p.F0[v] = 0;
+            p.F1[v] = 0;
+        }
+        for (int j = 0; j < g.k; ++j) {
+            int32_t* dp = sm.depth[j];
+            int32_t* pp = sm.parent[j];
+            for (long long v = gtid; v < g.n; v += gthreads) {
+                dp[v] = -1;
+                if (pp) pp[v] = -1;
+            }
+        }
+        if (gtid == 0) {
+            for (int s = 0; s < 3; ++s) {
+                ctl->slot[s].a_len = 0;
+                ctl->slot[s].u_len = 0;
+                ctl->slot[s].e_f = 0;
+                ctl->slot[s].work = 0;
+            }
+        }
+        if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+        if (blockIdx.x == 0 && threadIdx.x < (unsigned)g.k) {
+            int j = threadIdx.x;
+            int s = U->src[j];
+            atomicOr((unsigned long long*)p.seen + s, 1ull << j);
+            unsigned long long old = atomicOr((unsigned long long*)p.F0 + s, 1ull << j);
+            sm.depth[j][s] = 0;
+            if (sm.parent[j]) sm.parent[j][s] = s;
+            if (old == 0) {
+                int deg = g.row_ptr[s + 1] - g.row_ptr[s];
+                unsigned long long idx = atomicAdd(&ctl->slot[0].a_len, 1ull);
+                p.A0[idx] = s;
+                atomicAdd(&ctl->slot[0].e_f, (unsigned long long)deg);
+                if (deg >= p.chunk) {
+                    int nch = (deg + p.chunk - 1) / p.chunk;
+                    unsigned long long ub = atomicAdd(&ctl->slot[0].u_len, (unsigned long long)nch);
+                    if (ub + nch <= (unsigned long long)p.ucap)
+                        for (int c = 0; c < nch; ++c) p.U0[ub + c] = make_int2(s, c);
+                    else
+                        atomicCAS(&ctl->bar.err, 0, (int)DEV_OVERFLOW);
+                }
+            }
+        }
+        if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+        long long m_u = g.m, a_prev = 0;
+        int prev_dir = BFS_DIR_PUSH_QUEUE;
+        for (int level = 0;; ++level) {
+            CountersMS* cur = &ctl->slot[level % 3];
+            CountersMS* nxt = &ctl->slot[(level + 1) % 3];
+            long long a = (long long)__ldcg(&cur->a_len);
+            long long nunits = (long long)__ldcg(&cur->u_len);
+            long long e_f = (long long)__ldcg(&cur->e_f);
+            if (a == 0) break;
+            if (level >= p.max_levels) {
+                if (gtid == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
+                return;
+            }
+            m_u = max(m_u - e_f, 1ll);
+            int dir = ms_decide(p, g, sm, level, a, e_f, m_u, a_prev, prev_dir, deg_max);
+            if (gtid == 0) {
+                CountersMS* z = &ctl->slot[(level + 2) % 3];
+                z->a_len = 0;
+                z->u_len = 0;
+                z->e_f = 0;
+                z->work = 0;
+            }
+            const int32_t* a_cur = (level & 1) ? p.A1 : p.A0;
+            const int2* u_cur = (level & 1) ? p.U1 : p.U0;
+            uint64_t* f_cur = (level & 1) ? p.F1 : p.F0;
+            MsLevel L;
+            L.level = level;
+            L.f_next = (level & 1) ? p.F0 : p.F1;
+            L.a_next = (level & 1) ? p.A0 : p.A1;
+            L.u_next = (level & 1) ? p.U0 : p.U1;
+            L.next = nxt;
+            L.ef = 0;
+            if (dir == BFS_DIR_PULL) ms_pull_level(p, g, L, sm, f_cur);
+            else ms_push_level<T>(p, g, L, sm, a_cur, u_cur, f_cur, a, nunits, nxt);
+            unsigned long long ef = warp_sum(L.ef);
+            if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = ef;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long t = 0;
+                for (int i = 0; i < T / 32; ++i) t += sm.red[i];
+                if (t) atomicAdd(&nxt->e_f, t);
+            }
+            if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+            // F_i is consumed: clear its masks (they become the next target);
+            // after a push level, fold F_{i+1} into seen.
+            for (long long q = gtid; q < a; q += gthreads) f_cur[__ldcg(a_cur + q)] = 0;
+            if (dir != BFS_DIR_PULL) {
+                long long an = (long long)__ldcg(&nxt->a_len);
+                for (long long q = gtid; q < an; q += gthreads) {
+                    int v = __ldcg(L.a_next + q);
+                    p.seen[v] |= __ldcg((const unsigned long long*)L.f_next + v);
+                }
+            }
+            if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+            a_prev = a;
+            prev_dir = dir;
+            ++total_levels;
+        }
+    }
+    if (gtid == 0) ctl->levels = total_levels;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) msbfs_kernel(ParamsMS p) {
+    msbfs_body<T>(p);
+    if (threadIdx.x == 0) {
+        int e = ld_volatile_i32(&p.ctl->bar.err);
+        if (e) atomicCAS(p.sticky, 0, e);
+    }
+}
+
+constexpr int MS_T = 512;
+
+__global__ void ms_count_units_kernel(const int32_t* row_ptr, int32_t n, int32_t chunk, unsigned long long* out) {
+    unsigned long long s = 0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        int d = row_ptr[v + 1] - row_ptr[v];
+        if (d >= chunk) s += (unsigned long long)((d + chunk - 1) / chunk);
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+static int64_t count_units(const bfs_graph* g, int32_t chunk, cudaStream_t st) {
+    unsigned long long* d = nullptr;
+    unsigned long long h = 0;
+    if (cudaMallocAsync(&d, 8, st) != cudaSuccess) return -1;
+    cudaMemsetAsync(d, 0, 8, st);
+    ms_count_units_kernel<<<num_sms() * 8, 256, 0, st>>>(g->row_ptr, g->n, chunk, d);
+    cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    return (int64_t)h;
+}
+
+static bfs_status alloc_wsms(int32_t ncap, int64_t ucap, int32_t chunk, int32_t units_cap, WorkspaceMS** out) {
+    WorkspaceMS* w = new (std::nothrow) WorkspaceMS();
+    if (!w) return fail(BFS_ENOMEM, "host allocation");
+    w->ncap = ncap;
+    w->ucap = ucap;
+    w->chunk = chunk;
+    w->units_cap = units_cap;
+    bool ok = cudaMalloc(&w->seen, (size_t)ncap * 8) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = cudaMalloc(&w->front[i], (size_t)ncap * 8) == cudaSuccess &&
+             cudaMalloc(&w->act[i], (size_t)ncap * 4) == cudaSuccess &&
+             cudaMalloc(&w->U[i], (size_t)ucap * sizeof(int2)) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->ctl, sizeof(CtlMS)) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->d_sticky, 4) == cudaSuccess && cudaMemset(w->d_sticky, 0, 4) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->d_units, sizeof(MsUnit) * (size_t)units_cap) == cudaSuccess;
+    ok = ok && cudaMallocHost(&w->h_ctl, sizeof(CtlMS)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_wsms(w);
+        return fail(BFS_ENOMEM, "MS-BFS workspace for n=%d", ncap);
+    }
+    *out = w;
+    return BFS_OK;
+}
+
+static int coop_blocks_ms(int blocks_per_sm) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel<MS_T>, MS_T, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
+    return per_sm * num_sms();
+}
+
+static MsUnit make_unit(const bfs_graph* g) {
+    MsUnit u;
+    memset(&u, 0, sizeof(u));
+    u.row_ptr = g->row_ptr;
+    u.col = g->col;
+    u.csc_ptr = g->csc_ptr;
+    u.csc_col = g->csc_col;
+    u.isolated = g->isolated;
+    u.m = g->m;
+    u.n = g->n;
+    u.symmetric = g->symmetric;
+    u.deg_max = g->deg_max;
+    return u;
+}
+
+static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, const bfs_options& o, const float* mlp,
+                            const int8_t* d_sched, cudaStream_t st) {
+    if ((int32_t)units.size() > w->units_cap) return fail(BFS_EINVAL, "too many units");
+    BFS_CUDA(cudaMemcpyAsync(w->d_units, units.data(), sizeof(MsUnit) * units.size(), cudaMemcpyHostToDevice, st));
+    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(CtlMS), st));
+    ParamsMS p{};
+    p.units = w->d_units;
+    p.n_units = (int32_t)units.size();
+    p.seen = w->seen;
+    p.F0 = w->front[0];
+    p.F1 = w->front[1];
+    p.A0 = w->act[0];
+    p.A1 = w->act[1];
+    p.U0 = w->U[0];
+    p.U1 = w->U[1];
+    p.ucap = w->ucap;
+    p.ctl = w->ctl;
+    p.sticky = w->d_sticky;
+    p.policy = o.policy;
+    p.alpha = o.alpha;
+    p.beta = o.beta;
+    p.schedule = d_sched;
+    p.schedule_len = o.schedule_len;
+    p.mlp = mlp;
+    p.chunk = o.chunk;
+    p.medium = o.medium;
+    p.pull_serial = std::max(o.pull_serial, 1);
+    p.timeout_ns = o.barrier_timeout_ns;
+    p.max_levels = o.max_levels > 0 ? o.max_levels : INT32_MAX / 2;
+    int blocks = coop_blocks_ms(o.blocks_per_sm);
+    void* args[] = {(void*)&p};
+    BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, 0, st));
+    return BFS_OK;
+}
+
+// k sources over one graph, in units of 64 lanes; depth/parent: [k][n].
+bfs_status run_msbfs(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* depth, int32_t* parent,
+                     const bfs_options& o, const float* mlp_dev, cudaStream_t st) {
+    int32_t nunits = (int32_t)div_up(k, 64);
+    WorkspaceMS* w = g->wsms;
+    if (!w || w->chunk != o.chunk || w->units_cap < nunits) {
+        if (w) {
+            BFS_CUDA(cudaStreamSynchronize(st));
+            free_wsms(w);
+            g->wsms = nullptr;
+        }
+        int64_t uc = count_units(g, o.chunk, st);
+        if (uc < 0) return fail(BFS_ECUDA, "unit count");
+        bfs_status s = alloc_wsms(g->n, uc + 64, o.chunk, std::max(nunits, 4), &w);
+        if (s != BFS_OK) return s;
+        g->wsms = w;
+    }
+    const int64_t n = g->n;
+    bool dev_out = is_device_ptr(depth) && (!parent || is_device_ptr(parent));
+    int32_t *dd = depth, *dp = parent;
+    if (!dev_out) {
+        if (cudaMallocAsync(&dd, (size_t)k * n * 4, st) != cudaSuccess ||
+            (parent && cudaMallocAsync(&dp, (size_t)k * n * 4, st) != cudaSuccess)) {
+            cudaGetLastError();
+            return fail(BFS_ENOMEM, "staging outputs for %d sources", k);
+        }
+    }
+    int8_t* d_sched = nullptr;
+    if (o.policy == BFS_POLICY_SCHEDULE) {
+        if (!o.schedule || o.schedule_len <= 0) return fail(BFS_EINVAL, "schedule policy needs a schedule");
+        BFS_CUDA(cudaMallocAsync(&d_sched, o.schedule_len, st));
+        BFS_CUDA(cudaMemcpyAsync(d_sched, o.schedule, o.schedule_len, cudaMemcpyHostToDevice, st));
+    }
+    std::vector<MsUnit> units;
+    for (int32_t u0 = 0; u0 < k; u0 += 64) {
+        MsUnit u = make_unit(g);
+        u.k = std::min(64, k - u0);
+        for (int j = 0; j < u.k; ++j) {
+            u.src[j] = sources[u0 + j];
+            u.depth[j] = dd + (int64_t)(u0 + j) * n;
+            u.parent[j] = dp ? dp + (int64_t)(u0 + j) * n : nullptr;
+        }
+        units.push_back(u);
+    }
+    bfs_status s = launch_ms(w, units, o, mlp_dev, d_sched, st);
+    if (d_sched) cudaFreeAsync(d_sched, st);
+    if (s == BFS_OK && o.levels_out) {
+        BFS_CUDA(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(CtlMS), cudaMemcpyDeviceToHost, st));
+        BFS_CUDA(cudaStreamSynchronize(st));
+        *o.levels_out = w->h_ctl->levels;
+    }
+    if (!dev_out) {
+        cudaError_t e = cudaSuccess;
+        if (s == BFS_OK) e = cudaMemcpyAsync(depth, dd, (size_t)k * n * 4, cudaMemcpyDeviceToHost, st);
+        if (s == BFS_OK && e == cudaSuccess && parent) e = cudaMemcpyAsync(parent, dp, (size_t)k * n * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFreeAsync(dd, st);
+        if (dp) cudaFreeAsync(dp, st);
+        if (s == BFS_OK && e != cudaSuccess) s = cuda_fail(e, "copy outputs to host");
+        if (s == BFS_OK) {
+            int err = msbfs_sticky_error(g);
+            if (err) s = device_error(err, o.barrier_timeout_ns);
+        }
+    }
+    return s;
+}
+
+// Queries over several graphs in one launch: grouped per graph, 64 lanes a unit.
+bfs_status run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
+                     const int32_t* sources, int32_t nq, int32_t* const* depth, int32_t* const* parent,
+                     const bfs_options& o, cudaStream_t st) {
+    std::map<int, std::vector<int>> by_graph;
+    for (int q = 0; q < nq; ++q) by_graph[graph_of_query[q]].push_back(q);
+    std::vector<MsUnit> units;
+    int32_t ncap = 1;
+    int64_t ucap = 1;
+    for (auto& kv : by_graph) {
+        const bfs_graph* g = graphs[kv.first];
+        ncap = std::max(ncap, g->n);
+        int64_t uc = count_units(g, o.chunk, st);
+        if (uc < 0) return fail(BFS_ECUDA, "unit count");
+        ucap = std::max(ucap, uc + 64);
+        const std::vector<int>& qs = kv.second;
+        for (size_t i = 0; i < qs.size(); i += 64) {
+            MsUnit u = make_unit(g);
+            u.k = (int32_t)std::min<size_t>(64, qs.size() - i);
+            for (int j = 0; j < u.k; ++j) {
+                int q = qs[i + j];
+                u.src[j] = sources[q];
+                u.depth[j] = depth[q];
+                u.parent[j] = parent ? parent[q] : nullptr;
+            }
+            units.push_back(u);
+        }
+    }
+    WorkspaceMS* w = nullptr;
+    bfs_status s = alloc_wsms(ncap, ucap, o.chunk, (int32_t)units.size(), &w);
+    if (s != BFS_OK) return s;
+    int8_t* d_sched = nullptr;
+    if (o.policy == BFS_POLICY_SCHEDULE && o.schedule && o.schedule_len > 0) {
+        if (cudaMalloc(&d_sched, o.schedule_len) == cudaSuccess)
+            cudaMemcpy(d_sched, o.schedule, o.schedule_len, cudaMemcpyHostToDevice);
+    }
+    bfs_options oo = o;
+    if (oo.policy == BFS_POLICY_SCHEDULE && !d_sched) oo.policy = BFS_POLICY_HEURISTIC;
+    const float* mlp = nullptr;
+    if (oo.policy == BFS_POLICY_MLP && oo.mlp) mlp = policy_device_weights(oo.mlp);
+    s = launch_ms(w, units, oo, mlp, d_sched, st);
+    if (s == BFS_OK) {
+        cudaError_t e = cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(CtlMS), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "mixed batch");
+        else if (w->h_ctl->bar.err) s = device_error(w->h_ctl->bar.err, o.barrier_timeout_ns);
+        if (s == BFS_OK && o.levels_out) *o.levels_out = w->h_ctl->levels;
+    } else {
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(d_sched);
+    free_wsms(w);
+    return s;
+}
+
+}  // namespace bfsgb

@@ -1,0 +1,76 @@
+// policy_dev.cuh -- per-level features and the FP32 MLP evaluation used by the
+// learned direction policy inside the level loop.
+//
+// Parameter layout (floats, row-major):
+//   W1[32][10] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]   (1491)
+//   mean[10] inv_std[10]                                   (20, input normalisation)
+#pragma once
+
+#include <math.h>
+#include "../../include/bfs.h"
+
+namespace bfsgb {
+
+constexpr int MLP_IN = BFS_MLP_IN, MLP_H = BFS_MLP_HIDDEN, MLP_OUT = BFS_MLP_OUT;
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + MLP_H * MLP_IN;
+constexpr int OFF_W2 = OFF_B1 + MLP_H;
+constexpr int OFF_B2 = OFF_W2 + MLP_H * MLP_H;
+constexpr int OFF_W3 = OFF_B2 + MLP_H;
+constexpr int OFF_B3 = OFF_W3 + MLP_OUT * MLP_H;
+constexpr int NPARAM = OFF_B3 + MLP_OUT;
+constexpr int OFF_MEAN = NPARAM;
+constexpr int OFF_ISTD = NPARAM + MLP_IN;
+constexpr int NWEIGHTS = NPARAM + 2 * MLP_IN;
+static_assert(NPARAM == BFS_MLP_NPARAM, "parameter count");
+
+// Ten per-level features: log2 sizes of the frontier, its edges and the
+// unexplored edges, graph size, level, densities, degree spread, previous form.
+__host__ __device__ inline void policy_features(float* x, long long f, long long e_f, long long m_u, int level,
+                                                int prev_dir, int n, float log_n, float log_m, float log_degmax) {
+    x[0] = log2f(1.0f + (float)f);
+    x[1] = log2f(1.0f + (float)e_f);
+    x[2] = log2f(1.0f + (float)(m_u > 0 ? m_u : 0));
+    x[3] = log_n;
+    x[4] = log_m;
+    x[5] = log2f(1.0f + (float)level);
+    x[6] = (float)f / (float)n;
+    float r = (float)e_f / (float)(m_u > 1 ? m_u : 1);
+    x[7] = r < 64.0f ? r : 64.0f;
+    x[8] = log_degmax;
+    x[9] = (prev_dir == BFS_DIR_PULL) ? 1.0f : 0.0f;
+}
+
+#ifdef __CUDACC__
+// Warp-cooperative forward pass (lane j owns hidden unit j); returns the
+// argmax class (lowest index on ties) on every lane.  x: 10 raw features.
+__device__ inline int policy_argmax_warp(const float* __restrict__ w, const float* x) {
+    const unsigned lane = threadIdx.x & 31;
+    float xn[MLP_IN];
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) xn[k] = (x[k] - w[OFF_MEAN + k]) * w[OFF_ISTD + k];
+    float h1 = w[OFF_B1 + lane];
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) h1 = fmaf(w[OFF_W1 + lane * MLP_IN + k], xn[k], h1);
+    h1 = fmaxf(h1, 0.0f);
+    float h2 = w[OFF_B2 + lane];
+#pragma unroll 8
+    for (int k = 0; k < MLP_H; ++k) h2 = fmaf(w[OFF_W2 + lane * MLP_H + k], __shfl_sync(0xffffffffu, h1, k), h2);
+    h2 = fmaxf(h2, 0.0f);
+    float z[MLP_OUT];
+#pragma unroll
+    for (int c = 0; c < MLP_OUT; ++c) {
+        float t = w[OFF_W3 + c * MLP_H + lane] * h2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        z[c] = t + w[OFF_B3 + c];
+    }
+    int best = 0;
+#pragma unroll
+    for (int c = 1; c < MLP_OUT; ++c)
+        if (z[c] > z[best]) best = c;
+    return best;
+}
+#endif
+
+}  // namespace bfsgb

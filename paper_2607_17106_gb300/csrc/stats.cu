@@ -1,0 +1,152 @@
+// stats.cu -- per-level work statistics of a finished search (measurement
+// utility for the roofline model; not on the timed path).
+//
+// For a depth array of Cascade 1 the per-level quantities are
+//   f_i   = |F_i|,   e_f_i = sum deg over F_i,   d_new_i = |F_{i+1}|,
+//   u_i   = non-isolated v with depth > i or unreached, e_u_i their degree sum,
+//   s_u_i = entries a pull level reads: each such row scanned in ascending
+//           order up to the first neighbour of depth i, else completely.
+// A reached vertex of depth d has all neighbours at depth d-1, d or d+1, so
+// its row is scanned completely at every level i < d-1 and up to the first
+// depth-(d-1) neighbour at level d-1; unreached rows are always scanned
+// completely.  Hence s_u_i = e_u_i - sum_{v in F_{i+1}} (deg v - p_v), with
+// p_v the 1-based position of v's first depth-(d-1) neighbour, which makes
+// the whole table O(n + m) instead of O(levels * m).  The shortcut holds for
+// symmetric graphs (the configuration every benchmark uses).
+#include "common.cuh"
+
+#include <vector>
+
+namespace bfsgb {
+namespace {
+
+__global__ void max_depth_kernel(const int32_t* depth, int32_t n, int* out) {
+    int mx = -1;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, depth[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+// arrays: [5][L] = f, e_f, diff_u, diff_eu, corr ; consts: [2] = unreached count, unreached degree sum
+template <bool SMEM>
+__global__ void level_accum_kernel(const int32_t* row_ptr, const int32_t* col, const int32_t* depth, int32_t n, int L,
+                                   unsigned long long* arrays, unsigned long long* consts) {
+    extern __shared__ unsigned long long sh[];
+    unsigned long long* acc = SMEM ? sh : arrays;
+    if (SMEM) {
+        for (int i = threadIdx.x; i < 5 * L; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    unsigned long long un = 0, undeg = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int d = depth[v];
+        int b = row_ptr[v], e = row_ptr[v + 1];
+        unsigned long long deg = (unsigned long long)(e - b);
+        if (d < 0) {
+            if (deg > 0) {
+                ++un;
+                undeg += deg;
+            }
+            continue;
+        }
+        atomicAdd(&acc[0 * L + d], 1ull);
+        atomicAdd(&acc[1 * L + d], deg);
+        if (d >= 1 && deg > 0) {
+            // unvisited at levels 0 .. d-1
+            atomicAdd(&acc[2 * L + 0], 1ull);
+            atomicAdd(&acc[3 * L + 0], deg);
+            if (d < L) {
+                atomicAdd(&acc[2 * L + d], (unsigned long long)-1ll);
+                atomicAdd(&acc[3 * L + d], (unsigned long long)(-(long long)deg));
+            }
+            long long pv = 0;
+            for (int j = b; j < e; ++j) {
+                ++pv;
+                if (depth[col[j]] == d - 1) break;
+            }
+            atomicAdd(&acc[4 * L + (d - 1)], deg - (unsigned long long)pv);
+        }
+    }
+    un = warp_sum(un);
+    undeg = warp_sum(undeg);
+    if ((threadIdx.x & 31) == 0) {
+        if (un) atomicAdd(&consts[0], un);
+        if (undeg) atomicAdd(&consts[1], undeg);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 5 * L; i += blockDim.x)
+            if (sh[i]) atomicAdd(&arrays[i], sh[i]);
+    }
+}
+
+}  // namespace
+}  // namespace bfsgb
+
+using namespace bfsgb;
+
+extern "C" bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
+                                      int32_t* levels, void* cuda_stream) {
+    if (!g || !depth || !stats || max_levels <= 0) return fail(BFS_EINVAL, "null argument or max_levels <= 0");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int32_t* d_depth = depth;
+    int32_t* tmp_depth = nullptr;
+    if (!is_device_ptr(depth)) {
+        BFS_CUDA(cudaMallocAsync(&tmp_depth, (size_t)g->n * 4, st));
+        BFS_CUDA(cudaMemcpyAsync(tmp_depth, depth, (size_t)g->n * 4, cudaMemcpyHostToDevice, st));
+        d_depth = tmp_depth;
+    }
+    int* d_max;
+    BFS_CUDA(cudaMallocAsync(&d_max, 4, st));
+    int h_max = -1;
+    BFS_CUDA(cudaMemcpyAsync(d_max, &h_max, 4, cudaMemcpyHostToDevice, st));
+    int blocks = num_sms() * 4;
+    max_depth_kernel<<<blocks, 256, 0, st>>>(d_depth, g->n, d_max);
+    BFS_CUDA(cudaMemcpyAsync(&h_max, d_max, 4, cudaMemcpyDeviceToHost, st));
+    BFS_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_max, st);
+    int L = h_max + 1;
+    bfs_status rc = BFS_OK;
+    if (L > max_levels) {
+        if (tmp_depth) cudaFreeAsync(tmp_depth, st);
+        return fail(BFS_ERANGE, "search has %d levels, max_levels = %d", L, max_levels);
+    }
+    if (levels) *levels = L;
+    if (L <= 0) {
+        if (tmp_depth) cudaFreeAsync(tmp_depth, st);
+        return BFS_OK;
+    }
+    unsigned long long *d_arr, *d_const;
+    BFS_CUDA(cudaMallocAsync(&d_arr, (size_t)5 * L * 8, st));
+    BFS_CUDA(cudaMallocAsync(&d_const, 16, st));
+    BFS_CUDA(cudaMemsetAsync(d_arr, 0, (size_t)5 * L * 8, st));
+    BFS_CUDA(cudaMemsetAsync(d_const, 0, 16, st));
+    size_t sm = (size_t)5 * L * 8;
+    if (sm <= 48 * 1024) {
+        level_accum_kernel<true><<<blocks, 256, sm, st>>>(g->row_ptr, g->col, d_depth, g->n, L, d_arr, d_const);
+    } else {
+        level_accum_kernel<false><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, d_depth, g->n, L, d_arr, d_const);
+    }
+    std::vector<unsigned long long> arr((size_t)5 * L), cst(2);
+    BFS_CUDA(cudaMemcpyAsync(arr.data(), d_arr, arr.size() * 8, cudaMemcpyDeviceToHost, st));
+    BFS_CUDA(cudaMemcpyAsync(cst.data(), d_const, 16, cudaMemcpyDeviceToHost, st));
+    BFS_CUDA(cudaStreamSynchronize(st));
+    cudaFreeAsync(d_arr, st);
+    cudaFreeAsync(d_const, st);
+    if (tmp_depth) cudaFreeAsync(tmp_depth, st);
+    long long u = 0, eu = 0;
+    for (int i = 0; i < L; ++i) {
+        u += (long long)arr[2 * L + i];
+        eu += (long long)arr[3 * L + i];
+        int64_t* o = stats + 6 * (int64_t)i;
+        o[0] = (int64_t)arr[0 * L + i];
+        o[1] = (int64_t)arr[1 * L + i];
+        o[2] = u + (long long)cst[0];
+        o[5] = eu + (long long)cst[1];
+        o[3] = o[5] - (long long)arr[4 * L + i];
+        o[4] = (i + 1 < L) ? (int64_t)arr[0 * L + i + 1] : 0;
+    }
+    return rc;
+}

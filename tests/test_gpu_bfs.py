@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA path against the CPU oracle, through the C ABI.
+
+Depths must match the oracle bit-exactly (depth is the unique hop distance of
+Cascade 1); parents are not unique (ANY in Eq. advance), so they must pass the
+oracle's validator instead.  Every direction schedule must give the same depths
+(the paper's manipulations are semantics-preserving, Section 4.A).
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+import paper_2607_17106_gb300 as bg
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2607_17106_gb300 import build
+    build.build()
+    bg.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _graph_pair(n, src, dst):
+    adj = oracle.build_adjacency(n, src, dst)
+    g = bg.Graph.build(n, src, dst)
+    return adj, g
+
+
+def _run(g, n, sources, opt=None, with_parent=True):
+    k = len(sources)
+    depth = torch.empty(k * n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(k * n, dtype=torch.int32, device="cuda") if with_parent else None
+    src = np.asarray(sources, np.int32)
+    g.run(src, depth, parent, opt)
+    g.sync()
+    torch.cuda.synchronize()
+    d = depth.cpu().numpy().reshape(k, n)
+    p = parent.cpu().numpy().reshape(k, n) if with_parent else None
+    return d, p
+
+
+def _check(adj, sources, d, p):
+    for j, s in enumerate(sources):
+        ref, _ = oracle.bfs(adj, int(s), with_parent=False)
+        assert np.array_equal(d[j], ref), f"depth mismatch for source {s}: {np.flatnonzero(d[j] != ref)[:10]}"
+        if p is not None:
+            assert oracle.validate(adj, int(s), d[j], p[j]) == 0
+
+
+# ------------------------------------------------------------------ builder
+@pytest.mark.parametrize("kind", ["rmat", "er", "grid", "ba", "dups"])
+def test_builder_csr_equals_oracle_adjacency(kind):
+    if kind == "rmat":
+        n, s, d = graphgen.rmat(14, 16, seed=1)
+    elif kind == "er":
+        n, s, d = graphgen.erdos_renyi(30000, 100000, seed=3)
+    elif kind == "grid":
+        n, s, d = graphgen.grid(300, 200, 0.1, seed=4)
+    elif kind == "ba":
+        n, s, d = graphgen.barabasi_albert(20000, 8, seed=8)
+    else:
+        rng = np.random.default_rng(1)
+        n = 1000
+        s = rng.integers(0, 50, 20000).astype(np.int32)  # many repeats and self-loops
+        d = rng.integers(0, 50, 20000).astype(np.int32)
+    adj, g = _graph_pair(n, s, d)
+    rp, col = g.csr()
+    assert np.array_equal(rp.astype(np.int64), adj.row_ptr)
+    assert np.array_equal(col, adj.col)
+    info = g.info()
+    deg = np.diff(adj.row_ptr)
+    assert info.m == adj.m and info.deg_max == deg.max() and info.n_isolated == int((deg == 0).sum())
+    assert abs(info.deg_mean - deg.mean()) < 1e-9 * max(1, deg.mean())
+
+
+def test_builder_directed_csc_is_the_transpose():
+    n, s, d = graphgen.rmat(12, 8, seed=21)
+    adj = oracle.build_adjacency(n, s, d, symmetrize=False)
+    adjt = oracle.build_adjacency(n, d, s, symmetrize=False)
+    g = bg.Graph.build(n, s, d, flags=bg.BFS_DEDUP | bg.BFS_DROP_SELF | bg.BFS_BUILD_CSC)
+    rp, col = g.csr()
+    assert np.array_equal(rp, adj.row_ptr) and np.array_equal(col, adj.col)
+    rpt, colt = g.csr(csc=True)
+    assert np.array_equal(rpt, adjt.row_ptr) and np.array_equal(colt, adjt.col)
+    srcs = graphgen.sample_sources(n, s, d, 8, seed=3)
+    for policy in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH):
+        dd, pp = _run(g, n, srcs, bg.options(policy=policy, batch=0))
+        _check(adj, srcs, dd, pp)
+
+
+def test_builder_device_inputs_and_errors():
+    n, s, d = graphgen.rmat(10, 8, seed=2)
+    ts, td = torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()
+    g = bg.Graph.build(n, ts, td)
+    adj = oracle.build_adjacency(n, s, d)
+    rp, col = g.csr()
+    assert np.array_equal(col, adj.col)
+    bad = d.copy()
+    bad[5] = n
+    with pytest.raises(bg.BfsError) as e:
+        bg.Graph.build(n, s, bad)
+    assert e.value.status == bg.BFS_EINVAL
+
+
+# ----------------------------------------------------------- single source
+def _rmat14():
+    w = graphgen.WORKLOADS["rmat-s14-ef16"]
+    n, s, d = w.edges()
+    return n, s, d, w.sources(n, s, d)
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    n, s, d, srcs = _rmat14()
+    adj, g = _graph_pair(n, s, d)
+    return n, adj, g, srcs
+
+
+def test_rmat14_push_only_matches_oracle(rmat14):
+    n, adj, g, srcs = rmat14
+    d, p = _run(g, n, srcs, bg.options(policy=bg.BFS_POLICY_PUSH, batch=0))
+    _check(adj, srcs, d, p)
+
+
+@pytest.mark.parametrize("policy", [bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH])
+@pytest.mark.parametrize("mode", [bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_HOST_LOOP])
+def test_rmat14_policies_and_modes(rmat14, policy, mode):
+    n, adj, g, srcs = rmat14
+    d, p = _run(g, n, srcs[:6], bg.options(policy=policy, mode=mode, batch=0))
+    _check(adj, srcs[:6], d, p)
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("aggregate", [0, 1])
+def test_rmat14_launch_shapes_and_claiming(rmat14, threads, aggregate):
+    n, adj, g, srcs = rmat14
+    o = bg.options(block_threads=threads, claim_aggregate=aggregate, chunk=64, medium=8, batch=0)
+    d, p = _run(g, n, srcs[:4], o)
+    _check(adj, srcs[:4], d, p)
+
+
+def test_random_schedules_give_identical_depths(rmat14):
+    n, adj, g, srcs = rmat14
+    rng = np.random.default_rng(5)
+    for t in range(12):
+        sched = rng.integers(0, 3, 40).tolist()
+        s = srcs[t % len(srcs)]
+        d, p = _run(g, n, [s], bg.options(schedule=sched, chunk=128 if t % 2 else 2048, batch=0))
+        _check(adj, [s], d, p)
+
+
+def test_host_outputs_and_level_log(rmat14):
+    n, adj, g, srcs = rmat14
+    k = 3
+    depth = np.empty(k * n, np.int32)
+    parent = np.empty(k * n, np.int32)
+    log = (bg.bfs_level_record * 64)()
+    nlev = bg.ctypes.c_int32(0)
+    o = bg.options(batch=0, level_log=log, level_log_cap=64, levels_out=bg.ctypes.pointer(nlev))
+    g.run(np.asarray(srcs[:k], np.int32), depth, parent, o)
+    d, p = depth.reshape(k, n), parent.reshape(k, n)
+    _check(adj, srcs[:k], d, p)
+    ref = oracle.level_stats(adj, d[k - 1])
+    assert nlev.value == len(ref)
+    for i in range(nlev.value):
+        assert log[i].level == i and log[i].f == ref[i][0] and log[i].e_f == ref[i][1]
+
+
+@pytest.mark.parametrize("kind", ["er", "grid", "ba", "path", "star"])
+def test_other_graph_families(kind):
+    if kind == "er":
+        n, s, d = graphgen.erdos_renyi(1 << 15, 8 << 15, seed=3)
+    elif kind == "grid":
+        n, s, d = graphgen.grid(256, 256, 0.1, seed=4)
+    elif kind == "ba":
+        n, s, d = graphgen.barabasi_albert(1 << 15, 8, seed=8)
+    elif kind == "path":
+        n = 5000
+        s, d = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+    else:
+        n = 70000
+        s, d = np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32)
+    adj, g = _graph_pair(n, s, d)
+    srcs = graphgen.sample_sources(n, s, d, 4, seed=11)
+    for o in (bg.options(batch=0), bg.options(batch=0, chunk=64, medium=4, pull_serial=2)):
+        dd, pp = _run(g, n, srcs, o)
+        _check(adj, srcs, dd, pp)
+
+
+def test_edge_cases_tiny_and_isolated():
+    # one vertex, no edges
+    g = bg.Graph.build(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    d, p = _run(g, 1, [0], bg.options(batch=0))
+    assert d.tolist() == [[0]] and p.tolist() == [[0]]
+    # isolated source and disconnected pieces, n not a multiple of 32
+    n = 77
+    s = np.array([0, 1, 2, 40, 41, 76], np.int32)
+    dd = np.array([1, 2, 3, 41, 42, 76], np.int32)
+    adj, g = _graph_pair(n, s, dd)
+    for src in [0, 5, 40, 76]:
+        for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH):
+            d1, p1 = _run(g, n, [src], bg.options(policy=pol, batch=0))
+            _check(adj, [src], d1, p1)
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [n], bg.options(batch=0))
+    assert e.value.status == bg.BFS_EINVAL
+    with pytest.raises(bg.BfsError):
+        _run(g, n, [-1], bg.options(batch=0))
+
+
+def test_level_limit_and_barrier_timeout_report_errors(rmat14):
+    n, adj, g, srcs = rmat14
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [srcs[0]], bg.options(batch=0, max_levels=1))
+    assert e.value.status == bg.BFS_ERANGE
+    # a 1 ns limit makes every barrier wait run out: the kernel must give up
+    # cleanly and report ETIMEOUT, and the next run must be unaffected
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [srcs[0]], bg.options(batch=0, barrier_timeout_ns=1))
+    assert e.value.status == bg.BFS_ETIMEOUT
+    d, p = _run(g, n, srcs[:2], bg.options(batch=0))
+    _check(adj, srcs[:2], d, p)
+
+
+def test_level_stats_match_oracle(rmat14):
+    n, adj, g, srcs = rmat14
+    d, _ = _run(g, n, srcs[:3], bg.options(batch=0), with_parent=False)
+    for j in range(3):
+        ref = oracle.level_stats(adj, d[j])
+        got = g.level_stats(torch.from_numpy(d[j].copy()).cuda())
+        assert np.array_equal(got, ref)
+    n2 = 3000
+    pth, g2 = _graph_pair(n2, np.arange(n2 - 1, dtype=np.int32), np.arange(1, n2, dtype=np.int32))
+    d2, _ = _run(g2, n2, [0], bg.options(batch=0), with_parent=False)
+    assert np.array_equal(g2.level_stats(d2[0]), oracle.level_stats(pth, d2[0]))
+
+
+# ------------------------------------------------------------------ MS-BFS
+@pytest.mark.parametrize("k", [1, 5, 64, 130])
+def test_msbfs_lanes_match_single_source_oracle(rmat14, k):
+    n, adj, g, srcs = rmat14
+    w = graphgen.WORKLOADS["rmat-s14-ef16"]
+    _, s, d = w.edges()
+    sources = graphgen.sample_sources(n, s, d, k, seed=77)
+    dd, pp = _run(g, n, sources, bg.options(batch=1))
+    _check(adj, sources, dd, pp)
+
+
+@pytest.mark.parametrize("policy", [bg.BFS_POLICY_PUSH, bg.BFS_POLICY_PULL])
+def test_msbfs_forms_and_duplicate_sources(rmat14, policy):
+    n, adj, g, srcs = rmat14
+    sources = list(srcs[:10]) + list(srcs[:3])  # repeated sources are allowed
+    dd, pp = _run(g, n, sources, bg.options(policy=policy, chunk=64, medium=8, pull_serial=2))
+    _check(adj, sources, dd, pp)
+
+
+def test_msbfs_other_families():
+    for n, s, d in (graphgen.grid(128, 128, 0.1, seed=4), graphgen.erdos_renyi(20000, 80000, seed=5),
+                    graphgen.barabasi_albert(20000, 4, seed=6)):
+        adj, g = _graph_pair(n, s, d)
+        sources = graphgen.sample_sources(n, s, d, 64, seed=2)
+        dd, pp = _run(g, n, sources, bg.options())
+        _check(adj, sources, dd, pp)
+
+
+def test_mixed_batch_over_several_graphs():
+    graphs, adjs, ns = [], [], []
+    for sc in (10, 11, 12):
+        n, s, d = graphgen.rmat(sc, 8, seed=100 + sc)
+        adj, g = _graph_pair(n, s, d)
+        graphs.append(g)
+        adjs.append((adj, s, d))
+        ns.append(n)
+    rng = np.random.default_rng(4)
+    q = 150
+    goq = rng.integers(0, 3, q).astype(np.int32)
+    srcs = np.array([graphgen.sample_sources(ns[gi], adjs[gi][1], adjs[gi][2], 1, seed=1000 + i)[0]
+                     for i, gi in enumerate(goq)], np.int32)
+    depth = [torch.empty(ns[gi], dtype=torch.int32, device="cuda") for gi in goq]
+    parent = [torch.empty(ns[gi], dtype=torch.int32, device="cuda") for gi in goq]
+    bg.run_mixed(graphs, goq, srcs, depth, parent, bg.options())
+    torch.cuda.synchronize()
+    for i, gi in enumerate(goq):
+        adj = adjs[gi][0]
+        ref, _ = oracle.bfs(adj, int(srcs[i]), with_parent=False)
+        dd = depth[i].cpu().numpy()
+        assert np.array_equal(dd, ref)
+        assert oracle.validate(adj, int(srcs[i]), dd, parent[i].cpu().numpy()) == 0
