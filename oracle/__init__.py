@@ -61,7 +61,7 @@ def _load():
         lib.or_apsp_boolean.restype = ctypes.c_int
         lib.or_components.argtypes = [i64, i64, vp, vp, vp]
         lib.or_components.restype = ctypes.c_int
-        lib.or_validate.argtypes = [i64, vp, vp, ctypes.c_int32, vp, vp]
+        lib.or_validate.argtypes = [i64, vp, vp, ctypes.c_int32, vp, vp, ctypes.c_int]
         lib.or_validate.restype = ctypes.c_int
         lib.or_mlp_num_params.argtypes = []
         lib.or_mlp_num_params.restype = ctypes.c_int32
@@ -150,11 +150,11 @@ def components(n, src, dst) -> np.ndarray:
     return comp
 
 
-def validate(adj: Adjacency, s, depth, parent=None) -> int:
+def validate(adj: Adjacency, s, depth, parent=None, directed=False) -> int:
     depth = np.ascontiguousarray(depth, np.int32)
     parent = None if parent is None else np.ascontiguousarray(parent, np.int32)
     return int(_load().or_validate(adj.n, _ptr(adj.row_ptr), _ptr(adj.col), int(s), _ptr(depth),
-                                   _ptr(parent)))
+                                   _ptr(parent), int(directed)))
 
 
 def mlp_num_params() -> int:

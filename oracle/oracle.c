@@ -259,9 +259,12 @@ static int has_edge(const int64_t* row_ptr, const int32_t* col, int32_t a, int32
  *   8 a vertex other than s has depth 0 or depth < -1
  * Pass parent = NULL to check only the depth conditions.  Returns 0 if valid.
  * Rows must be sorted (for the edge lookup).
+ * With `directed`, conditions 3 and 4 follow the edge direction only (a
+ * directed edge is the tuple (s,d) of Section 3): for an edge (u,v) with u
+ * reached, v is reached (4) and depth v <= depth u + 1 (3).
  */
 int or_validate(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t s, const int32_t* depth,
-                const int32_t* parent) {
+                const int32_t* parent, int directed) {
     if (depth[s] != 0) return 1;
     if (parent && parent[s] != s) return 1;
     for (int64_t v = 0; v < n; ++v) {
@@ -272,6 +275,11 @@ int or_validate(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t s
         for (int64_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
             int32_t v = col[j];
             int ru = depth[u] >= 0, rv = depth[v] >= 0;
+            if (directed) {
+                if (ru && !rv) return 4;
+                if (ru && depth[v] > depth[u] + 1) return 3;
+                continue;
+            }
             if (ru != rv) return 4;
             if (ru && rv && abs(depth[u] - depth[v]) > 1) return 3;
         }

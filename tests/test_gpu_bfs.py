@@ -44,12 +44,12 @@ def _run(g, n, sources, opt=None, with_parent=True):
     return d, p
 
 
-def _check(adj, sources, d, p):
+def _check(adj, sources, d, p, directed=False):
     for j, s in enumerate(sources):
         ref, _ = oracle.bfs(adj, int(s), with_parent=False)
         assert np.array_equal(d[j], ref), f"depth mismatch for source {s}: {np.flatnonzero(d[j] != ref)[:10]}"
         if p is not None:
-            assert oracle.validate(adj, int(s), d[j], p[j]) == 0
+            assert oracle.validate(adj, int(s), d[j], p[j], directed=directed) == 0
 
 
 # ------------------------------------------------------------------ builder
@@ -90,7 +90,9 @@ def test_builder_directed_csc_is_the_transpose():
     srcs = graphgen.sample_sources(n, s, d, 8, seed=3)
     for policy in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH):
         dd, pp = _run(g, n, srcs, bg.options(policy=policy, batch=0))
-        _check(adj, srcs, dd, pp)
+        _check(adj, srcs, dd, pp, directed=True)
+    dd, pp = _run(g, n, srcs, bg.options(batch=1))
+    _check(adj, srcs, dd, pp, directed=True)
 
 
 def test_builder_device_inputs_and_errors():

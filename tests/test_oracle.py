@@ -284,3 +284,18 @@ def test_adam_first_step_is_lr_times_sign():
     g = np.array([0.3, -5.0, 1e-3])
     oracle.adam_step(P, m1, m2, g, t=1, lr=0.01, eps=1e-12)
     assert np.allclose(P, [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01], atol=1e-9)
+
+
+def test_directed_validation_follows_edge_direction():
+    # 0 -> 1 -> 2 -> 0 cycle plus 2 -> 3: from 0, depth(0)=0 is reached again by 2 -> 0
+    src = np.array([0, 1, 2, 2], np.int32)
+    dst = np.array([1, 2, 0, 3], np.int32)
+    adj = oracle.build_adjacency(4, src, dst, symmetrize=False)
+    depth, parent = oracle.bfs(adj, 0)
+    assert depth.tolist() == [0, 1, 2, 3]
+    assert oracle.validate(adj, 0, depth, parent, directed=True) == 0
+    assert oracle.validate(adj, 0, depth, parent, directed=False) == 3   # 2 -> 0 spans two levels
+    d = depth.copy(); d[3] = -1
+    assert oracle.validate(adj, 0, d, None, directed=True) == 4
+    d = depth.copy(); d[3] = 5
+    assert oracle.validate(adj, 0, d, None, directed=True) == 3
