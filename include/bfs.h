@@ -130,7 +130,7 @@ typedef struct {
     float alpha;             /* Beamer alpha (14) */
     float beta;              /* Beamer beta (24) */
     float gamma;             /* push levels read the bitmap when f > n / gamma (16) */
-    int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (2048) */
+    int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (256) */
     int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
     int32_t pull_serial;     /* pull: entries one thread scans before a warp takes over (8) */
     int32_t block_threads;   /* threads per CTA of the level kernels (512) */

@@ -22,7 +22,7 @@
 // new bits of P and of F_{i+1} are written with plain stores.
 //
 // Load balance (push): vertices with degree >= `chunk` are split at claim time
-// into chunk-edge units that whole CTAs take from a work counter; the rest of
+// into chunk-edge units that whole CTAs take round-robin; the rest of
 // the frontier is cut into CTA tiles; inside a tile, degree >= `medium` goes
 // to a whole warp and smaller rows are flattened over the CTA by a block scan
 // of degrees (the flatten/partition mappings of Section 7.2.1).
@@ -46,7 +46,7 @@ struct Counters {
     unsigned long long q_len;  // vertices appended to the next queue (= |F_{i+1}|)
     unsigned long long u_len;  // chunk units appended for the next level
     unsigned long long e_f;    // sum of out-degrees of the appended vertices
-    unsigned long long work;   // work counter of the level that fills this slot
+    unsigned long long conv;   // cursor of a bitmap -> queue conversion of this frontier
 };
 
 struct Ctl1 {
@@ -56,6 +56,7 @@ struct Ctl1 {
     int32_t next_level;
     int32_t prev_dir;
     int32_t bm_valid;   // level whose frontier bitmap is current, -1 if none
+    int32_t q_valid;    // level whose frontier queue (and chunk units) is current
     int32_t done;
     long long m_u;
     long long f_prev;
@@ -188,39 +189,58 @@ __device__ int decide_dir(const Params1& p, int level, long long f, long long e_
 }
 
 // ------------------------------------------------------------ claiming
+constexpr int QBUF = 64;  // per-warp shared-memory staging of next-queue entries
+
 struct LevelCtx {
-    int32_t level;         // i: discovered vertices get depth i+1
+    int32_t level;          // i: discovered vertices get depth i+1
     int32_t* q_next;
     int2* u_next;
-    Counters* next;        // counters of F_{i+1}
-    unsigned long long ef; // this thread's share of e_f(F_{i+1})
+    Counters* next;         // counters of F_{i+1}
+    unsigned long long ef;  // this thread's share of e_f(F_{i+1})
+    unsigned long long cnt; // this thread's share of |F_{i+1}| (pull levels)
+    int32_t* qbuf;          // this warp's staging buffer (QBUF entries)
+    int qn;                 // entries staged (warp-uniform)
 };
 
-// Record claimed vertices: depth/parent, next-queue slot (warp-aggregated),
-// degree sum, and chunk units for big rows.  Warp-uniform call.
+// Move the warp's staged queue entries to the next queue: one atomic per
+// flush instead of one per claiming round.  Warp-uniform.
+__device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
+    if (L.qn == 0) return;
+    unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&L.next->q_len, (unsigned long long)L.qn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = L.qbuf[i];
+    __syncwarp();
+    L.qn = 0;
+}
+
+__device__ __forceinline__ void emit_units(const Params1& p, int2* u_out, Counters* c, int v, int deg) {
+    int nch = (deg + p.chunk - 1) / p.chunk;
+    unsigned long long ub = atomicAdd(&c->u_len, (unsigned long long)nch);
+    if (ub + nch <= (unsigned long long)p.ucap) {
+        for (int k = 0; k < nch; ++k) u_out[ub + k] = make_int2(v, k);
+    } else {
+        atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
+    }
+}
+
+// Record vertices claimed in a push level: depth/parent, staged next-queue
+// slot, degree sum, chunk units for big rows.  Warp-uniform call.
 __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int deg) {
     unsigned cm = __ballot_sync(0xffffffffu, claimed);
     if (!cm) return;
-    unsigned lane = lane_id();
-    int leader = __ffs(cm) - 1;
-    unsigned long long base = 0;
-    if ((int)lane == leader) base = atomicAdd(&L.next->q_len, (unsigned long long)__popc(cm));
-    base = __shfl_sync(0xffffffffu, base, leader);
+    int c = __popc(cm);
+    if (L.qn + c > QBUF) flush_qbuf(L);
     if (claimed) {
-        L.q_next[base + __popc(cm & lanemask_lt())] = v;
+        L.qbuf[L.qn + __popc(cm & lanemask_lt())] = v;
         p.depth[v] = L.level + 1;
         if (p.parent) p.parent[v] = u;
         L.ef += (unsigned long long)deg;
-        if (deg >= p.chunk) {
-            int nch = (deg + p.chunk - 1) / p.chunk;
-            unsigned long long ub = atomicAdd(&L.next->u_len, (unsigned long long)nch);
-            if (ub + nch <= (unsigned long long)p.ucap) {
-                for (int c = 0; c < nch; ++c) L.u_next[ub + c] = make_int2(v, c);
-            } else {
-                atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-            }
-        }
+        if (deg >= p.chunk) emit_units(p, L.u_next, L.next, v, deg);
     }
+    L.qn += c;
 }
 
 // Push candidate (u -> v): claim v in P if not yet visited.  Warp-uniform.
@@ -262,18 +282,21 @@ struct TileSmem {
     int beg[T];
     int src[T];
     int scan_tmp[33];
-    int item;
+    int32_t qbuf[(T / 32) * QBUF];
+    unsigned long long red[T / 32];
+    unsigned long long base;
 };
 
 // One CTA expands up to T frontier vertices (one per thread, u < 0 = none).
+// Rows of degree >= chunk are skipped when chunk units cover them.
 template <int T>
-__device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int u) {
+__device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int u, bool skip_big) {
     unsigned lane = lane_id();
     int beg = 0, end = 0;
     if (u >= 0) {
         beg = __ldg(p.row_ptr + u);
         end = __ldg(p.row_ptr + u + 1);
-        if (end - beg >= p.chunk) end = beg;  // covered by chunk units
+        if (skip_big && end - beg >= p.chunk) end = beg;
     }
     // medium rows: one warp each
     bool med = (end - beg) >= p.medium;
@@ -333,21 +356,18 @@ __device__ __forceinline__ void push_unit(const Params1& p, LevelCtx& L, int2 un
     }
 }
 
-// Push level: work items are [units of F_i] then [tiles of the frontier],
-// handed out by the level's work counter.
+// Push level: items are [chunk units of F_i] then [tiles of the frontier],
+// dealt to CTAs round-robin (units are equal-sized; tiles hold rows below
+// the chunk size).
 template <int T>
 __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int32_t* q_cur,
-                           const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, Counters* work) {
+                           const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, bool units_valid) {
     long long ntiles;
     if (dir == BFS_DIR_PUSH_QUEUE) ntiles = (f + T - 1) / T;
     else ntiles = (p.W + (T / 32) - 1) / (T / 32);
+    if (!units_valid) nunits = 0;
     long long nitems = nunits + ntiles;
-    while (true) {
-        if (threadIdx.x == 0) sm.item = (int)atomicAdd(&work->work, 1ull);
-        __syncthreads();
-        long long it = sm.item;
-        __syncthreads();
-        if (it >= nitems) break;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
         if (it < nunits) {
             push_unit<T>(p, L, __ldcg(u_cur + it));
         } else {
@@ -363,33 +383,24 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
                     if ((fw >> (threadIdx.x & 31)) & 1u) u = (int)(w * 32 + (threadIdx.x & 31));
                 }
             }
-            push_tile<T>(p, L, sm, u);
+            push_tile<T>(p, L, sm, u, units_valid);
         }
     }
+    flush_qbuf(L);
 }
 
 // ------------------------------------------------------------ pull level
-__device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next) {
+// Finish one 32-vertex word w (lane = vertex) whose first in-neighbour was
+// already tested: continue the ascending scan thread-serially for up to
+// pull_serial entries, then warp-cooperatively for long rows; write the word
+// of P and of F_{i+1}; count the new vertices and their degrees.
+__device__ __forceinline__ void pull_finish(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                            long long w, unsigned pw, bool unvis, int j, int end, bool found, int par,
+                                            int deg) {
     unsigned lane = lane_id();
-    long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long w = gwarp; w < p.W; w += nwarps) {
-        unsigned pw = __ldcg(p.P + w);
-        long long v = w * 32 + lane;
-        bool unvis = v < p.n && !((pw >> lane) & 1u);
-        if (!__ballot_sync(0xffffffffu, unvis)) {
-            if (lane == 0) f_next[w] = 0;
-            continue;
-        }
-        int beg = 0, end = 0;
-        if (unvis) {
-            beg = __ldg(p.csc_ptr + v);
-            end = __ldg(p.csc_ptr + v + 1);
-        }
-        bool found = false;
-        int par = -1;
-        int lim = min(end, beg + p.pull_serial);
-        for (int j = beg; j < lim; ++j) {
+    int lim = min(end, j + p.pull_serial);
+    if (unvis && !found) {
+        for (; j < lim; ++j) {
             int u = __ldg(p.csc_col + j);
             if ((__ldcg(f_cur + (u >> 5)) >> (u & 31)) & 1u) {
                 found = true;
@@ -397,40 +408,125 @@ __device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
                 break;
             }
         }
-        unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && lim < end);
-        while (rm) {
-            int l = __ffs(rm) - 1;
-            int bl = __shfl_sync(0xffffffffu, lim, l);
-            int el = __shfl_sync(0xffffffffu, end, l);
-            int hit = -1;
-            for (int base = bl; base < el; base += 32) {
-                int idx = base + (int)lane;
-                int uu = 0;
-                bool h = false;
-                if (idx < el) {
-                    uu = __ldg(p.csc_col + idx);
-                    h = (__ldcg(f_cur + (uu >> 5)) >> (uu & 31)) & 1u;
-                }
-                unsigned hb = __ballot_sync(0xffffffffu, h);
-                if (hb) {
-                    hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                    break;
+    }
+    unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && lim < end);
+    while (rm) {
+        int l = __ffs(rm) - 1;
+        int bl = __shfl_sync(0xffffffffu, lim, l);
+        int el = __shfl_sync(0xffffffffu, end, l);
+        int hit = -1;
+        for (int base = bl; base < el; base += 32) {
+            int idx = base + (int)lane;
+            int uu = 0;
+            bool h = false;
+            if (idx < el) {
+                uu = __ldg(p.csc_col + idx);
+                h = (__ldcg(f_cur + (uu >> 5)) >> (uu & 31)) & 1u;
+            }
+            unsigned hb = __ballot_sync(0xffffffffu, h);
+            if (hb) {
+                hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
+                break;
+            }
+        }
+        if ((int)lane == l && hit >= 0) {
+            found = true;
+            par = hit;
+        }
+        rm &= rm - 1;
+    }
+    unsigned nb = __ballot_sync(0xffffffffu, found);
+    if (lane == 0) {
+        f_next[w] = nb;
+        if (nb) p.P[w] = pw | nb;
+    }
+    if (found) {
+        long long v = w * 32 + lane;
+        p.depth[v] = L.level + 1;
+        if (p.parent) p.parent[v] = par;
+        if (!p.symmetric) deg = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
+        L.ef += (unsigned long long)deg;
+        L.cnt += 1;
+    }
+}
+
+constexpr int PULL_ILP = 4;
+
+// Pull level: each warp reads 32 words of P with one coalesced load, writes
+// F_{i+1} = 0 for the fully visited ones, and handles the others PULL_ILP at
+// a time so that their row-offset, first-column and frontier-bit loads are in
+// flight together.
+__device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next) {
+    unsigned lane = lane_id();
+    long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
+        long long wl = wb + lane;
+        unsigned pw = wl < p.W ? __ldcg(p.P + wl) : 0xffffffffu;
+        if (wl < p.W && pw == 0xffffffffu) f_next[wl] = 0;
+        unsigned todo = __ballot_sync(0xffffffffu, pw != 0xffffffffu);
+        while (todo) {
+            int wi[PULL_ILP];
+            unsigned pwi[PULL_ILP];
+#pragma unroll
+            for (int k = 0; k < PULL_ILP; ++k) {
+                if (todo) {
+                    wi[k] = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    pwi[k] = __shfl_sync(0xffffffffu, pw, wi[k]);
+                } else {
+                    wi[k] = -1;
+                    pwi[k] = 0xffffffffu;
                 }
             }
-            if ((int)lane == l && hit >= 0) {
-                found = true;
-                par = hit;
+            int beg[PULL_ILP], end[PULL_ILP], u0[PULL_ILP];
+            bool unvis[PULL_ILP], found[PULL_ILP];
+#pragma unroll
+            for (int k = 0; k < PULL_ILP; ++k) {
+                unvis[k] = !((pwi[k] >> lane) & 1u);
+                long long v = (wb + wi[k]) * 32 + lane;
+                beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
+                end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
             }
-            rm &= rm - 1;
+#pragma unroll
+            for (int k = 0; k < PULL_ILP; ++k) u0[k] = beg[k] < end[k] ? __ldg(p.csc_col + beg[k]) : -1;
+#pragma unroll
+            for (int k = 0; k < PULL_ILP; ++k)
+                found[k] = u0[k] >= 0 && ((__ldcg(f_cur + (u0[k] >> 5)) >> (u0[k] & 31)) & 1u);
+#pragma unroll
+            for (int k = 0; k < PULL_ILP; ++k) {
+                if (wi[k] < 0) break;  // warp-uniform
+                pull_finish(p, L, f_cur, f_next, wb + wi[k], pwi[k], unvis[k], beg[k] + 1, end[k], found[k],
+                            u0[k], end[k] - beg[k]);
+            }
         }
-        unsigned nb = __ballot_sync(0xffffffffu, found);
-        if (lane == 0) {
-            f_next[w] = nb;
-            if (nb) p.P[w] = pw | nb;
+    }
+}
+
+// ------------------------------------------------------------ conversions
+// F_i bitmap -> queue Q_i (ascending vertex order inside each CTA chunk) and
+// chunk units for its big rows.  Cursor: cur->conv.
+template <int T>
+__device__ void bitmap_to_queue(const Params1& p, TileSmem<T>& sm, const uint32_t* f_cur, int32_t* q_cur, int2* u_cur,
+                                Counters* cur) {
+    for (long long wb = (long long)blockIdx.x * T; wb < p.W; wb += (long long)gridDim.x * T) {
+        long long w = wb + threadIdx.x;
+        unsigned fw = w < p.W ? __ldcg(f_cur + w) : 0u;
+        int c = __popc(fw), total;
+        int off = block_exclusive_scan(c, sm.scan_tmp, &total);
+        if (threadIdx.x == 0 && total) sm.base = atomicAdd(&cur->conv, (unsigned long long)total);
+        __syncthreads();
+        unsigned long long base = sm.base;
+        int r = 0;
+        while (fw) {
+            int b = __ffs(fw) - 1;
+            fw &= fw - 1;
+            int v = (int)(w * 32 + b);
+            q_cur[base + off + r++] = v;
+            int deg = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
+            if (deg >= p.chunk) emit_units(p, u_cur, cur, v, deg);
         }
-        int deg = 0;
-        if (found) deg = p.symmetric ? (end - beg) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
-        emit(p, L, found, (int)v, par, deg);
+        __syncthreads();
     }
 }
 
@@ -440,7 +536,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
-    __shared__ unsigned long long s_red[T / 32];
     Ctl1* ctl = p.ctl;
     const unsigned nblocks = gridDim.x;
     const long long gtid = (long long)blockIdx.x * T + threadIdx.x;
@@ -451,6 +546,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         for (long long w = gtid; w < p.W; w += gthreads) {
             unsigned bits = __ldg(p.isolated + w);
             if (w == (s >> 5)) bits |= 1u << (s & 31);
+            if (w == p.W - 1 && (p.n & 31)) bits |= ~((1u << (p.n & 31)) - 1u);  // phantom vertices
             p.P[w] = bits;
         }
         for (long long v = gtid; v < p.n; v += gthreads) {
@@ -468,6 +564,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             ctl->next_level = 0;
             ctl->prev_dir = BFS_DIR_PUSH_QUEUE;
             ctl->bm_valid = -1;
+            ctl->q_valid = 0;
             ctl->done = 0;
             ctl->m_u = p.m - deg;
             ctl->f_prev = 0;
@@ -478,10 +575,12 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     int level = __ldcg(&ctl->next_level);
     int prev_dir = __ldcg(&ctl->prev_dir);
     int bm_valid = __ldcg(&ctl->bm_valid);
+    int q_valid = __ldcg(&ctl->q_valid);
     long long m_u = __ldcg(&ctl->m_u);
     long long f_prev = __ldcg(&ctl->f_prev);
     bool done = __ldcg(&ctl->done) != 0;
     int level_end = level + p.level_count;
+    const unsigned warp = threadIdx.x >> 5;
 
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
@@ -510,8 +609,8 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             r.t_ns = (int64_t)globaltimer_ns();
             p.log[level] = r;
         }
-        const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
-        const int2* u_cur = (level & 1) ? p.U1 : p.U0;
+        int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
+        int2* u_cur = (level & 1) ? p.U1 : p.U0;
         uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
         uint32_t* f_nxt = (level & 1) ? p.F0 : p.F1;
         if (dir != BFS_DIR_PUSH_QUEUE && bm_valid != level) {
@@ -525,12 +624,19 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
             bm_valid = level;
         }
+        if (dir == BFS_DIR_PUSH_QUEUE && q_valid != level) {
+            // bitmap -> queue conversion of F_i (after pull levels)
+            bitmap_to_queue<T>(p, sm, f_cur, q_cur, u_cur, cur);
+            if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+            nunits = (long long)__ldcg(&cur->u_len);
+            q_valid = level;
+        }
         if (gtid == 0) {
             Counters* z = &ctl->slot[(level + 2) % 3];
             z->q_len = 0;
             z->u_len = 0;
             z->e_f = 0;
-            z->work = 0;
+            z->conv = 0;
         }
         LevelCtx L;
         L.level = level;
@@ -538,21 +644,37 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.u_next = (level & 1) ? p.U0 : p.U1;
         L.next = nxt;
         L.ef = 0;
+        L.cnt = 0;
+        L.qbuf = sm.qbuf + warp * QBUF;
+        L.qn = 0;
         if (dir == BFS_DIR_PULL) {
             pull_level(p, L, f_cur, f_nxt);
         } else {
-            push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, nxt);
+            push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
         }
-        // e_f of F_{i+1}: one atomic per CTA
+        // e_f (and |F_{i+1}| for pull) of the next frontier: one atomic per CTA
         unsigned long long ef = warp_sum(L.ef);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ef;
+        unsigned long long cn = warp_sum(L.cnt);
+        if ((threadIdx.x & 31) == 0) sm.red[warp] = ef;
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long t = 0;
-            for (int i = 0; i < T / 32; ++i) t += s_red[i];
+            for (int i = 0; i < T / 32; ++i) t += sm.red[i];
             if (t) atomicAdd(&nxt->e_f, t);
         }
-        if (dir == BFS_DIR_PULL) bm_valid = level + 1;
+        __syncthreads();
+        if (dir == BFS_DIR_PULL) {
+            if ((threadIdx.x & 31) == 0) sm.red[warp] = cn;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long t = 0;
+                for (int i = 0; i < T / 32; ++i) t += sm.red[i];
+                if (t) atomicAdd(&nxt->q_len, t);
+            }
+            bm_valid = level + 1;
+        } else {
+            q_valid = level + 1;
+        }
         prev_dir = dir;
         f_prev = f;
         ++level;
@@ -562,6 +684,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         ctl->next_level = level;
         ctl->prev_dir = prev_dir;
         ctl->bm_valid = bm_valid;
+        ctl->q_valid = q_valid;
         ctl->m_u = m_u;
         ctl->f_prev = f_prev;
         ctl->done = done ? 1 : 0;

@@ -85,7 +85,7 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->alpha = 14.0f;
     o->beta = 24.0f;
     o->gamma = 16.0f;
-    o->chunk = 2048;
+    o->chunk = 256;
     o->medium = 32;
     o->pull_serial = 8;
     o->block_threads = 512;

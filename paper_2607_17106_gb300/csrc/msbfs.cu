@@ -649,7 +649,7 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.mlp = mlp;
     p.chunk = o.chunk;
     p.medium = o.medium;
-    p.pull_serial = std::max(o.pull_serial, 1);
+    p.pull_serial = std::max(o.pull_serial, 1) * 8;  // lanes rarely all found early: longer serial scans
     p.timeout_ns = o.barrier_timeout_ns;
     p.max_levels = o.max_levels > 0 ? o.max_levels : INT32_MAX / 2;
     int blocks = coop_blocks_ms(o.blocks_per_sm);
