@@ -132,7 +132,7 @@ typedef struct {
     float gamma;             /* push levels read the bitmap when f > n / gamma (16) */
     int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (256) */
     int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
-    int32_t pull_serial;     /* pull: entries one thread scans before a warp takes over (8) */
+    int32_t pull_serial;     /* pull: entries of one row tested per flattened warp round (32; MS-BFS: twice this many entries are scanned per thread before a warp takes over) */
     int32_t block_threads;   /* threads per CTA of the level kernels (512) */
     int32_t blocks_per_sm;   /* CTAs per SM, 0 = as many as fit (persistent/cooperative launch) */
     int32_t claim_aggregate; /* push: warp-aggregate the visited-bitmap OR by word (1) */
@@ -141,7 +141,7 @@ typedef struct {
     int32_t schedule_len;
     int32_t max_levels;      /* stop with BFS_ERANGE after this many levels, 0 = n + 1 */
     const bfs_policy* mlp;   /* for BFS_POLICY_MLP */
-    bfs_level_record* level_log; /* optional host array, one record per level (k = 1 only) */
+    bfs_level_record* level_log; /* optional host array, one record per level (k > 1: first 64-lane unit) */
     int32_t level_log_cap;
     int32_t* levels_out;     /* optional host int32: number of levels executed (k = 1: last run) */
     int32_t batch;           /* k > 1: 1 = 64-lane MS-BFS batches (default), 0 = one source at a time */

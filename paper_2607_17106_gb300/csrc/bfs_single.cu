@@ -390,80 +390,178 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
 }
 
 // ------------------------------------------------------------ pull level
-// Finish one 32-vertex word w (lane = vertex) whose first in-neighbour was
-// already tested: continue the ascending scan thread-serially for up to
-// pull_serial entries, then warp-cooperatively for long rows; write the word
-// of P and of F_{i+1}; count the new vertices and their degrees.
-__device__ __forceinline__ void pull_finish(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                                            long long w, unsigned pw, bool unvis, int j, int end, bool found, int par,
-                                            int deg) {
-    unsigned lane = lane_id();
-    int lim = min(end, j + p.pull_serial);
-    if (unvis && !found) {
-        for (; j < lim; ++j) {
-            int u = __ldg(p.csc_col + j);
-            if ((__ldcg(f_cur + (u >> 5)) >> (u & 31)) & 1u) {
-                found = true;
-                par = u;
-                break;
-            }
-        }
+constexpr int PULL_ILP = 8;     // words a warp handles per step
+constexpr int PULL_BLOCK = 16;  // words of P a warp reads per block
+constexpr int PULL_LIST = 32 * PULL_ILP;  // leftover rows of one step (at most every row)
+
+// Per-warp shared memory of the pull level.
+struct PullSmem {
+    int v[PULL_LIST];     // leftover row: vertex
+    int j[PULL_LIST];     //   next position to test
+    int end[PULL_LIST];   //   row end
+    int off[PULL_LIST + 1];
+    unsigned hit[PULL_LIST];  // lowest hit position of this round, ~0u if none
+    unsigned word_nb[PULL_ILP];  // found bits per word of the step
+};
+
+// One pull step over up to PULL_ILP 32-vertex words (lane = vertex of each
+// word).  Phase 1: every unvisited row tests its first in-neighbour, all
+// rows' loads in flight together.  Phase 2: rows not yet resolved go to a
+// shared-memory list that the warp scans flattened: each round every live row
+// contributes up to `pull_serial` entries, a prefix over the list lays the
+// entries out over the lanes, and the lowest hit position of a row (a min in
+// shared memory) gives its parent.  Phase 3 writes the words of P and F_{i+1}.
+__device__ __forceinline__ void pull_step(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                          long long wb, const int (&wi)[PULL_ILP], const unsigned (&pwi)[PULL_ILP],
+                                          PullSmem& ps) {
+    const unsigned lane = lane_id();
+    const int dnext = L.level + 1;
+    int beg[PULL_ILP], end[PULL_ILP], u0[PULL_ILP];
+#pragma unroll
+    for (int k = 0; k < PULL_ILP; ++k) {
+        bool unvis = !((pwi[k] >> lane) & 1u);
+        long long v = (wb + wi[k]) * 32 + lane;
+        beg[k] = unvis ? __ldg(p.csc_ptr + v) : 0;
+        end[k] = unvis ? __ldg(p.csc_ptr + v + 1) : 0;
     }
-    unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && lim < end);
-    while (rm) {
-        int l = __ffs(rm) - 1;
-        int bl = __shfl_sync(0xffffffffu, lim, l);
-        int el = __shfl_sync(0xffffffffu, end, l);
-        int hit = -1;
-        for (int base = bl; base < el; base += 32) {
-            int idx = base + (int)lane;
-            int uu = 0;
-            bool h = false;
-            if (idx < el) {
-                uu = __ldg(p.csc_col + idx);
-                h = (__ldcg(f_cur + (uu >> 5)) >> (uu & 31)) & 1u;
-            }
-            unsigned hb = __ballot_sync(0xffffffffu, h);
-            if (hb) {
-                hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                break;
-            }
+#pragma unroll
+    for (int k = 0; k < PULL_ILP; ++k) u0[k] = (beg[k] < end[k]) ? __ldg(p.csc_col + beg[k]) : -1;
+    int nlist = 0;
+#pragma unroll
+    for (int k = 0; k < PULL_ILP; ++k) {
+        bool found = u0[k] >= 0 && ((__ldcg(f_cur + (u0[k] >> 5)) >> (u0[k] & 31)) & 1u);
+        long long v = (wb + wi[k]) * 32 + lane;
+        if (found) {
+            p.depth[v] = dnext;
+            if (p.parent) p.parent[v] = u0[k];
+            int dg = p.symmetric ? end[k] - beg[k] : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+            L.ef += (unsigned long long)dg;
+            L.cnt += 1;
         }
-        if ((int)lane == l && hit >= 0) {
-            found = true;
-            par = hit;
+        unsigned nb = __ballot_sync(0xffffffffu, found);
+        if (lane == 0) ps.word_nb[k] = nb;
+        bool left = u0[k] >= 0 && !found && beg[k] + 1 < end[k];
+        unsigned lm = __ballot_sync(0xffffffffu, left);
+        if (left) {
+            int r = nlist + __popc(lm & lanemask_lt());
+            ps.v[r] = (int)v;
+            ps.j[r] = beg[k] + 1;
+            ps.end[r] = end[k];
         }
-        rm &= rm - 1;
+        nlist += __popc(lm);
     }
-    unsigned nb = __ballot_sync(0xffffffffu, found);
-    if (lane == 0) {
+    __syncwarp();
+    const int cap = p.pull_serial;
+    while (nlist > 0) {
+        // contributions and their prefix (rows lane, lane+32, ...)
+        int loc = 0;
+        for (int r = (int)lane; r < nlist; r += 32) loc += min(ps.end[r] - ps.j[r], cap);
+        int incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        // per-lane rows are strided, so lay offsets out row by row
+        // (prefix in row order = sum over earlier rows): recompute serially
+        // per lane group of 32 rows
+        int run = 0;
+        for (int r0 = 0; r0 < nlist; r0 += 32) {
+            int r = r0 + (int)lane;
+            int c = r < nlist ? min(ps.end[r] - ps.j[r], cap) : 0;
+            int ci = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, ci, o);
+                if ((int)lane >= o) ci += y;
+            }
+            if (r < nlist) {
+                ps.off[r] = run + ci - c;
+                ps.hit[r] = ~0u;
+            }
+            run += __shfl_sync(0xffffffffu, ci, 31);
+        }
+        if (lane == 0) ps.off[nlist] = total;
+        __syncwarp();
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            int x = e0 + (int)lane;
+            if (x < total) {
+                int lo = 0, hi = nlist - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (ps.off[mid] <= x) lo = mid; else hi = mid - 1;
+                }
+                int pos = ps.j[lo] + (x - ps.off[lo]);
+                int u = __ldg(p.csc_col + pos);
+                if ((__ldcg(f_cur + (u >> 5)) >> (u & 31)) & 1u) atomicMin(&ps.hit[lo], (unsigned)pos);
+            }
+        }
+        __syncwarp();
+        // resolve rows; keep the live ones (compacted) for the next round
+        int keep = 0;
+        for (int r0 = 0; r0 < nlist; r0 += 32) {
+            int r = r0 + (int)lane;
+            bool live = false;
+            int rv = 0, rj = 0, re = 0;
+            if (r < nlist) {
+                rv = ps.v[r];
+                rj = ps.j[r];
+                re = ps.end[r];
+                unsigned h = ps.hit[r];
+                if (h != ~0u) {
+                    int par = __ldg(p.csc_col + h);
+                    p.depth[rv] = dnext;
+                    if (p.parent) p.parent[rv] = par;
+                    int dg = p.symmetric ? (__ldg(p.csc_ptr + rv + 1) - __ldg(p.csc_ptr + rv))
+                                         : (__ldg(p.row_ptr + rv + 1) - __ldg(p.row_ptr + rv));
+                    L.ef += (unsigned long long)dg;
+                    L.cnt += 1;
+                    long long w = rv >> 5;
+                    // the word's index within the step
+#pragma unroll
+                    for (int k = 0; k < PULL_ILP; ++k)
+                        if (wi[k] >= 0 && wb + wi[k] == w) atomicOr(&ps.word_nb[k], 1u << (rv & 31));
+                } else {
+                    rj += min(re - rj, cap);
+                    live = rj < re;
+                }
+            }
+            unsigned lm = __ballot_sync(0xffffffffu, live);
+            __syncwarp();
+            if (live) {
+                int q = keep + __popc(lm & lanemask_lt());
+                ps.v[q] = rv;
+                ps.j[q] = rj;
+                ps.end[q] = re;
+            }
+            keep += __popc(lm);
+            __syncwarp();
+        }
+        nlist = keep;
+    }
+    __syncwarp();
+    if ((int)lane < PULL_ILP && wi[lane] >= 0) {
+        long long w = wb + wi[lane];
+        unsigned nb = ps.word_nb[lane];
         f_next[w] = nb;
-        if (nb) p.P[w] = pw | nb;
+        if (nb) p.P[w] = pwi[lane] | nb;
     }
-    if (found) {
-        long long v = w * 32 + lane;
-        p.depth[v] = L.level + 1;
-        if (p.parent) p.parent[v] = par;
-        if (!p.symmetric) deg = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
-        L.ef += (unsigned long long)deg;
-        L.cnt += 1;
-    }
+    __syncwarp();
 }
 
-constexpr int PULL_ILP = 4;
-
-// Pull level: each warp reads 32 words of P with one coalesced load, writes
-// F_{i+1} = 0 for the fully visited ones, and handles the others PULL_ILP at
-// a time so that their row-offset, first-column and frontier-bit loads are in
-// flight together.
-__device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next) {
+// Pull level: each warp reads PULL_BLOCK words of P with one coalesced load,
+// writes F_{i+1} = 0 for the fully visited ones, and handles the others
+// PULL_ILP at a time.
+__device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next, PullSmem& ps) {
     unsigned lane = lane_id();
     long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
+    for (long long wb = gwarp * PULL_BLOCK; wb < p.W; wb += nwarps * PULL_BLOCK) {
         long long wl = wb + lane;
-        unsigned pw = wl < p.W ? __ldcg(p.P + wl) : 0xffffffffu;
-        if (wl < p.W && pw == 0xffffffffu) f_next[wl] = 0;
+        bool mine = lane < PULL_BLOCK && wl < p.W;
+        unsigned pw = mine ? __ldcg(p.P + wl) : 0xffffffffu;
+        if (mine && pw == 0xffffffffu) f_next[wl] = 0;
         unsigned todo = __ballot_sync(0xffffffffu, pw != 0xffffffffu);
         while (todo) {
             int wi[PULL_ILP];
@@ -479,26 +577,7 @@ __device__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
                     pwi[k] = 0xffffffffu;
                 }
             }
-            int beg[PULL_ILP], end[PULL_ILP], u0[PULL_ILP];
-            bool unvis[PULL_ILP], found[PULL_ILP];
-#pragma unroll
-            for (int k = 0; k < PULL_ILP; ++k) {
-                unvis[k] = !((pwi[k] >> lane) & 1u);
-                long long v = (wb + wi[k]) * 32 + lane;
-                beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
-                end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < PULL_ILP; ++k) u0[k] = beg[k] < end[k] ? __ldg(p.csc_col + beg[k]) : -1;
-#pragma unroll
-            for (int k = 0; k < PULL_ILP; ++k)
-                found[k] = u0[k] >= 0 && ((__ldcg(f_cur + (u0[k] >> 5)) >> (u0[k] & 31)) & 1u);
-#pragma unroll
-            for (int k = 0; k < PULL_ILP; ++k) {
-                if (wi[k] < 0) break;  // warp-uniform
-                pull_finish(p, L, f_cur, f_next, wb + wi[k], pwi[k], unvis[k], beg[k] + 1, end[k], found[k],
-                            u0[k], end[k] - beg[k]);
-            }
+            pull_step(p, L, f_cur, f_next, wb, wi, pwi, ps);
         }
     }
 }
@@ -534,6 +613,7 @@ __device__ void bitmap_to_queue(const Params1& p, TileSmem<T>& sm, const uint32_
 template <int T>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
+    __shared__ PullSmem s_pull[T / 32];
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
     Ctl1* ctl = p.ctl;
@@ -648,7 +728,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.qbuf = sm.qbuf + warp * QBUF;
         L.qn = 0;
         if (dir == BFS_DIR_PULL) {
-            pull_level(p, L, f_cur, f_nxt);
+            pull_level(p, L, f_cur, f_nxt, s_pull[warp]);
         } else {
             push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
         }
@@ -691,8 +771,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     }
 }
 
+// 64 registers a thread so that 1024 threads fit on an SM with the pull
+// level's shared memory (32 warps of memory-level parallelism).
 template <int T>
-__global__ void __launch_bounds__(T) bfs1_kernel(Params1 p) {
+__global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1) bfs1_kernel(Params1 p) {
     bfs1_body<T>(p);
     if (threadIdx.x == 0) {
         int e = ld_volatile_i32(&p.ctl->bar.err);

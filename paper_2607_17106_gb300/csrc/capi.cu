@@ -87,7 +87,7 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->gamma = 16.0f;
     o->chunk = 256;
     o->medium = 32;
-    o->pull_serial = 8;
+    o->pull_serial = 32;
     o->block_threads = 512;
     o->blocks_per_sm = 0;
     o->claim_aggregate = 1;
@@ -104,7 +104,7 @@ static bfs_status check_options(const bfs_options* in, bfs_options* o) {
     if (o->policy < 0 || o->policy > 4) return fail(BFS_EINVAL, "bad policy %d", o->policy);
     if (o->chunk < 64) return fail(BFS_EINVAL, "chunk must be >= 64");
     if (o->medium < 1) return fail(BFS_EINVAL, "medium must be >= 1");
-    if (o->pull_serial < 0) return fail(BFS_EINVAL, "pull_serial must be >= 0");
+    if (o->pull_serial < 1) return fail(BFS_EINVAL, "pull_serial must be >= 1");
     if (!(o->alpha > 0) || !(o->beta > 0) || !(o->gamma > 0)) return fail(BFS_EINVAL, "alpha, beta, gamma must be > 0");
     if (o->barrier_timeout_ns <= 0) return fail(BFS_EINVAL, "barrier_timeout_ns must be > 0");
     if (o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)

@@ -118,6 +118,8 @@ struct ParamsMS {
     int32_t chunk, medium, pull_serial;
     int64_t timeout_ns;
     int32_t max_levels;
+    bfs_level_record* log;  // per-level records of the first unit
+    int32_t log_cap;
 };
 
 // Unit fields kept in registers / shared memory while a unit runs.
@@ -495,6 +497,16 @@ __device__ void msbfs_body(const ParamsMS& p) {
             }
             m_u = max(m_u - e_f, 1ll);
             int dir = ms_decide(p, g, sm, level, a, e_f, m_u, a_prev, prev_dir, deg_max);
+            if (ui == 0 && gtid == 0 && p.log && level < p.log_cap) {
+                bfs_level_record r;
+                r.level = level;
+                r.dir = dir;
+                r.f = a;
+                r.e_f = e_f;
+                r.m_u = m_u;
+                r.t_ns = (int64_t)globaltimer_ns();
+                p.log[level] = r;
+            }
             if (gtid == 0) {
                 CountersMS* z = &ctl->slot[(level + 2) % 3];
                 z->a_len = 0;
@@ -624,7 +636,7 @@ static MsUnit make_unit(const bfs_graph* g) {
 }
 
 static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, const bfs_options& o, const float* mlp,
-                            const int8_t* d_sched, cudaStream_t st) {
+                            const int8_t* d_sched, cudaStream_t st, bfs_level_record* d_log = nullptr) {
     if ((int32_t)units.size() > w->units_cap) return fail(BFS_EINVAL, "too many units");
     BFS_CUDA(cudaMemcpyAsync(w->d_units, units.data(), sizeof(MsUnit) * units.size(), cudaMemcpyHostToDevice, st));
     BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(CtlMS), st));
@@ -649,9 +661,11 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.mlp = mlp;
     p.chunk = o.chunk;
     p.medium = o.medium;
-    p.pull_serial = std::max(o.pull_serial, 1) * 8;  // lanes rarely all found early: longer serial scans
+    p.pull_serial = std::max(o.pull_serial, 1) * 2;  // all missing lanes are rarely found early: longer serial scans
     p.timeout_ns = o.barrier_timeout_ns;
     p.max_levels = o.max_levels > 0 ? o.max_levels : INT32_MAX / 2;
+    p.log = d_log;
+    p.log_cap = d_log ? o.level_log_cap : 0;
     int blocks = coop_blocks_ms(o.blocks_per_sm);
     void* args[] = {(void*)&p};
     BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, 0, st));
@@ -702,8 +716,20 @@ bfs_status run_msbfs(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* d
         }
         units.push_back(u);
     }
-    bfs_status s = launch_ms(w, units, o, mlp_dev, d_sched, st);
+    bfs_level_record* d_log = nullptr;
+    if (o.level_log && o.level_log_cap > 0)
+        BFS_CUDA(cudaMallocAsync(&d_log, sizeof(bfs_level_record) * o.level_log_cap, st));
+    bfs_status s = launch_ms(w, units, o, mlp_dev, d_sched, st, d_log);
     if (d_sched) cudaFreeAsync(d_sched, st);
+    if (d_log) {
+        if (s == BFS_OK) {
+            BFS_CUDA(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(CtlMS), cudaMemcpyDeviceToHost, st));
+            BFS_CUDA(cudaStreamSynchronize(st));
+            int nl = std::min(w->h_ctl->levels, o.level_log_cap);
+            if (nl > 0) BFS_CUDA(cudaMemcpy(o.level_log, d_log, sizeof(bfs_level_record) * nl, cudaMemcpyDeviceToHost));
+        }
+        cudaFreeAsync(d_log, st);
+    }
     if (s == BFS_OK && o.levels_out) {
         BFS_CUDA(cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(CtlMS), cudaMemcpyDeviceToHost, st));
         BFS_CUDA(cudaStreamSynchronize(st));
