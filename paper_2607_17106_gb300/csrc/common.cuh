@@ -90,39 +90,35 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const vo
 
 // Grid barrier state: one per persistent launch (zeroed before launch).
 struct GridBarrier {
-    unsigned count;
-    unsigned gen;
-    int abort;    // set by any CTA that gives up; every waiter checks it
-    int err;      // DEV_* code of the first failure
+    unsigned count;  // CTA arrivals since the state was zeroed (monotonic)
+    int abort;       // set by any CTA that gives up; every waiter checks it
+    int err;         // DEV_* code of the first failure
+    unsigned pad;
 };
 
-// Barrier over `nblocks` co-resident CTAs (cooperative launch).  Spins on the
-// generation word with a %globaltimer limit; on expiry it records DEV_TIMEOUT,
-// raises the abort flag and returns false, so every CTA leaves its loop.
-// Returns false when the barrier was aborted (by this CTA or another).
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, int64_t timeout_ns) {
+// Barrier over `nblocks` co-resident CTAs (cooperative launch).  Each CTA
+// keeps the running arrival target in `target` (nblocks more per barrier);
+// thread 0 adds its arrival to the monotonic counter and waits until the
+// counter reaches the target, with a %globaltimer limit: on expiry it
+// records DEV_TIMEOUT, raises the abort flag and returns false, so every CTA
+// leaves its loop.  Returns false when the barrier was aborted.
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsigned& target, int64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
+    target += nblocks;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_acquire_u32(&b->gen);
         __threadfence();
-        unsigned arrived = atomicAdd(&b->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            st_release_u32(&b->gen, gen + 1);
-        } else {
-            uint64_t t0 = globaltimer_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u32(&b->gen) == gen) {
-                if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
-                if ((++spins & 63u) == 1 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) {
-                    atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);
-                    atomicExch(&b->abort, 1);
-                    ok = 0;
-                    break;
-                }
+        atomicAdd(&b->count, 1u);
+        const uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+            if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
+            if ((++spins & 63u) == 1 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) {
+                atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);
+                atomicExch(&b->abort, 1);
+                ok = 0;
+                break;
             }
         }
         if (ld_volatile_i32(&b->abort)) ok = 0;

@@ -416,6 +416,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
     const unsigned nblocks = gridDim.x;
     const long long gtid = (long long)blockIdx.x * T + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * T;
+    unsigned bar_target = 0;
     int total_levels = 0;
     for (int ui = 0; ui < p.n_units; ++ui) {
         const MsUnit* U = p.units + ui;
@@ -458,7 +459,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 ctl->slot[s].work = 0;
             }
         }
-        if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         if (blockIdx.x == 0 && threadIdx.x < (unsigned)g.k) {
             int j = threadIdx.x;
             int s = U->src[j];
@@ -481,7 +482,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 }
             }
         }
-        if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         long long m_u = g.m, a_prev = 0;
         int prev_dir = BFS_DIR_PUSH_QUEUE;
         for (int level = 0;; ++level) {
@@ -534,7 +535,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 for (int i = 0; i < T / 32; ++i) t += sm.red[i];
                 if (t) atomicAdd(&nxt->e_f, t);
             }
-            if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             // F_i is consumed: clear its masks (they become the next target);
             // after a push level, fold F_{i+1} into seen.
             for (long long q = gtid; q < a; q += gthreads) f_cur[__ldcg(a_cur + q)] = 0;
@@ -545,7 +546,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                     p.seen[v] |= __ldcg((const unsigned long long*)L.f_next + v);
                 }
             }
-            if (!grid_sync(&ctl->bar, nblocks, p.timeout_ns)) return;
+            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             a_prev = a;
             prev_dir = dir;
             ++total_levels;

@@ -130,7 +130,7 @@ def test_rmat14_push_only_matches_oracle(rmat14):
 
 
 @pytest.mark.parametrize("policy", [bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH])
-@pytest.mark.parametrize("mode", [bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_HOST_LOOP])
+@pytest.mark.parametrize("mode", [bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_HOST_LOOP, bg.BFS_MODE_GRAPH])
 def test_rmat14_policies_and_modes(rmat14, policy, mode):
     n, adj, g, srcs = rmat14
     d, p = _run(g, n, srcs[:6], bg.options(policy=policy, mode=mode, batch=0))
@@ -146,13 +146,14 @@ def test_rmat14_launch_shapes_and_claiming(rmat14, threads, aggregate):
     _check(adj, srcs[:4], d, p)
 
 
-def test_random_schedules_give_identical_depths(rmat14):
+@pytest.mark.parametrize("mode", [bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_GRAPH])
+def test_random_schedules_give_identical_depths(rmat14, mode):
     n, adj, g, srcs = rmat14
     rng = np.random.default_rng(5)
     for t in range(12):
         sched = rng.integers(0, 3, 40).tolist()
         s = srcs[t % len(srcs)]
-        d, p = _run(g, n, [s], bg.options(schedule=sched, chunk=128 if t % 2 else 2048, batch=0))
+        d, p = _run(g, n, [s], bg.options(schedule=sched, chunk=128 if t % 2 else 2048, batch=0, mode=mode))
         _check(adj, [s], d, p)
 
 
@@ -171,6 +172,14 @@ def test_host_outputs_and_level_log(rmat14):
     assert nlev.value == len(ref)
     for i in range(nlev.value):
         assert log[i].level == i and log[i].f == ref[i][0] and log[i].e_f == ref[i][1]
+    # the graph-mode loop records the same levels
+    log2 = (bg.bfs_level_record * 64)()
+    o = bg.options(batch=0, mode=bg.BFS_MODE_GRAPH, level_log=log2, level_log_cap=64,
+                   levels_out=bg.ctypes.pointer(nlev))
+    g.run(np.asarray(srcs[k - 1:k], np.int32), depth[:n], parent[:n], o)
+    assert nlev.value == len(ref)
+    for i in range(nlev.value):
+        assert log2[i].f == ref[i][0] and log2[i].e_f == ref[i][1]
 
 
 @pytest.mark.parametrize("kind", ["er", "grid", "ba", "path", "star"])
@@ -189,7 +198,8 @@ def test_other_graph_families(kind):
         s, d = np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32)
     adj, g = _graph_pair(n, s, d)
     srcs = graphgen.sample_sources(n, s, d, 4, seed=11)
-    for o in (bg.options(batch=0), bg.options(batch=0, chunk=64, medium=4, pull_serial=2)):
+    for o in (bg.options(batch=0), bg.options(batch=0, chunk=64, medium=4, pull_serial=2),
+              bg.options(batch=0, mode=bg.BFS_MODE_GRAPH)):
         dd, pp = _run(g, n, srcs, o)
         _check(adj, srcs, dd, pp)
 
@@ -206,8 +216,9 @@ def test_edge_cases_tiny_and_isolated():
     adj, g = _graph_pair(n, s, dd)
     for src in [0, 5, 40, 76]:
         for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PULL, bg.BFS_POLICY_PUSH):
-            d1, p1 = _run(g, n, [src], bg.options(policy=pol, batch=0))
-            _check(adj, [src], d1, p1)
+            for mode in (bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_GRAPH):
+                d1, p1 = _run(g, n, [src], bg.options(policy=pol, batch=0, mode=mode))
+                _check(adj, [src], d1, p1)
     with pytest.raises(bg.BfsError) as e:
         _run(g, n, [n], bg.options(batch=0))
     assert e.value.status == bg.BFS_EINVAL
@@ -219,6 +230,9 @@ def test_level_limit_and_barrier_timeout_report_errors(rmat14):
     n, adj, g, srcs = rmat14
     with pytest.raises(bg.BfsError) as e:
         _run(g, n, [srcs[0]], bg.options(batch=0, max_levels=1))
+    assert e.value.status == bg.BFS_ERANGE
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [srcs[0]], bg.options(batch=0, max_levels=1, mode=bg.BFS_MODE_GRAPH))
     assert e.value.status == bg.BFS_ERANGE
     # a 1 ns limit makes every barrier wait run out: the kernel must give up
     # cleanly and report ETIMEOUT, and the next run must be unaffected
