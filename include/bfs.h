@@ -219,6 +219,20 @@ bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max
 bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,
                                int32_t prev_dir, float* out10);
 
+/*
+ * Training signal of the policy: run the plain method (opt->policy, heuristic
+ * by default) from `source` one level at a time; before each level i, save
+ * the level state and time every form BFS_DIR_* from that same state
+ * (median of `repeats` launches, format conversions included), then continue
+ * with the plain method's own choice.  Host outputs, L = *levels rows each:
+ * features[L][10] (bfs_policy_features of the level), times_us[L][3],
+ * taken[L] (form the plain method used; may be NULL).  Synchronous.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT.
+ */
+bfs_status bfs_profile_levels(const bfs_graph* g, int32_t source, const bfs_options* opt, int32_t repeats,
+                              int32_t max_levels, float* features, float* times_us, int32_t* taken, int32_t* levels,
+                              void* cuda_stream);
+
 /* weights: host float[nw], nw = BFS_MLP_NPARAM + BFS_MLP_NNORM. */
 bfs_status bfs_policy_load(const float* weights, int32_t nw, bfs_policy** out);
 bfs_status bfs_policy_weights(const bfs_policy* p, float* out, int32_t nw); /* host copy */

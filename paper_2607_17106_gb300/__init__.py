@@ -35,7 +35,7 @@ BFS_MLP_NPARAM, BFS_MLP_NNORM = 1507, 20
 
 EXPORTED = [
     "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_free_graph", "bfs_options_init", "bfs_run",
-    "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_policy_features", "bfs_policy_load",
+    "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_profile_levels", "bfs_policy_features", "bfs_policy_load",
     "bfs_policy_weights", "bfs_policy_free", "bfs_policy_forward", "bfs_policy_train_step",
     "bfs_policy_set_norm", "bfs_status_string", "bfs_last_error", "bfs_version",
 ]
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
         "bfs_run_mixed": (st, [ctypes.POINTER(vp), i32, vp, vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                ctypes.POINTER(bfs_options), vp]),
         "bfs_level_stats": (st, [vp, vp, i32, vp, ctypes.POINTER(i32), vp]),
+        "bfs_profile_levels": (st, [vp, i32, ctypes.POINTER(bfs_options), i32, i32, vp, vp, vp,
+                                    ctypes.POINTER(i32), vp]),
         "bfs_policy_features": (st, [vp, i32, i64, i64, i64, i32, vp]),
         "bfs_policy_load": (st, [vp, i32, ctypes.POINTER(vp)]),
         "bfs_policy_weights": (st, [vp, vp, i32]),
@@ -220,6 +222,19 @@ class Graph:
         _check(load().bfs_level_stats(self.handle, _ptr(depth), int(max_levels), _ptr(out), ctypes.byref(lv),
                                       _stream(stream)))
         return out[: lv.value].copy()
+
+    def profile_levels(self, source: int, opt: bfs_options | None = None, repeats: int = 3,
+                       max_levels: int = 4096, stream=None):
+        """(features[L][10], times_us[L][3], taken[L]) of bfs_profile_levels."""
+        X = np.zeros((max_levels, BFS_MLP_IN), np.float32)
+        T = np.zeros((max_levels, 3), np.float32)
+        taken = np.zeros(max_levels, np.int32)
+        lv = ctypes.c_int32(0)
+        _check(load().bfs_profile_levels(self.handle, int(source), ctypes.byref(opt) if opt is not None else None,
+                                         int(repeats), int(max_levels), _ptr(X), _ptr(T), _ptr(taken),
+                                         ctypes.byref(lv), _stream(stream)))
+        L = lv.value
+        return X[:L].copy(), T[:L].copy(), taken[:L].copy()
 
     def features(self, level, f, e_f, m_u, prev_dir) -> np.ndarray:
         x = np.empty(BFS_MLP_IN, np.float32)

@@ -27,7 +27,6 @@ namespace {
 
 constexpr int GT = 512;        // threads of the push / conversion kernels
 constexpr int PULL_T = 256;    // threads of the pull kernel
-constexpr int PULL_SERIAL = 32;  // entries one lane scans before its warp takes over
 
 __global__ void __launch_bounds__(256) g_init(Params1 p, int32_t s, int32_t* depth, int32_t* parent) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -208,87 +207,25 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     }
 }
 
-// Pull level at full occupancy: one warp per 32-vertex word of P (lane =
-// vertex); each unvisited lane scans its in-neighbours in ascending order
-// and stops at the first one in F_i; rows longer than PULL_SERIAL entries are
-// finished by the whole warp 32 entries at a time.
+// Pull level at full occupancy (few registers): pull_level_words with
+// non-coherent loads of P and F_i, which no CTA writes during this kernel
+// except the word owner after its last read.
 __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     __shared__ unsigned long long s_ef[PULL_T / 32], s_cn[PULL_T / 32];
     Ctl1* ctl = p.ctl;
     const int level = ctl->cur_level;
+    LevelCtx L;
+    L.level = level;
+    L.depth = ctl->depth;
+    L.parent = ctl->parent;
+    L.ef = 0;
+    L.cnt = 0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     uint32_t* f_next = (level & 1) ? p.F0 : p.F1;
-    int32_t* depth = ctl->depth;
-    int32_t* parent = ctl->parent;
-    const unsigned lane = lane_id();
-    const long long nwarps = ((long long)gridDim.x * PULL_T) >> 5;
-    unsigned long long ef = 0, cn = 0;
-    for (long long w = ((long long)blockIdx.x * PULL_T + threadIdx.x) >> 5; w < p.W; w += nwarps) {
-        const unsigned pw = __ldcg(p.P + w);
-        if (pw == 0xffffffffu) {
-            if (lane == 0) f_next[w] = 0;
-            continue;
-        }
-        const long long v = w * 32 + lane;
-        const bool unvis = !((pw >> lane) & 1u);
-        int beg = 0, end = 0;
-        if (unvis) {
-            beg = __ldg(p.csc_ptr + v);
-            end = __ldg(p.csc_ptr + v + 1);
-        }
-        bool found = false;
-        int par = -1;
-        int j = beg;
-        const int lim = min(end, beg + PULL_SERIAL);
-        for (; j < lim; ++j) {
-            int u = __ldg(p.csc_col + j);
-            if ((__ldcg(f_cur + (u >> 5)) >> (u & 31)) & 1u) {
-                found = true;
-                par = u;
-                break;
-            }
-        }
-        unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && j < end);
-        while (rm) {
-            const int l = __ffs(rm) - 1;
-            const int bl = __shfl_sync(0xffffffffu, j, l);
-            const int el = __shfl_sync(0xffffffffu, end, l);
-            int hit = -1;
-            for (int base = bl; base < el; base += 32) {
-                int idx = base + (int)lane;
-                int uu = 0;
-                bool h = false;
-                if (idx < el) {
-                    uu = __ldg(p.csc_col + idx);
-                    h = (__ldcg(f_cur + (uu >> 5)) >> (uu & 31)) & 1u;
-                }
-                unsigned hb = __ballot_sync(0xffffffffu, h);
-                if (hb) {
-                    hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                    break;
-                }
-            }
-            if ((int)lane == l && hit >= 0) {
-                found = true;
-                par = hit;
-            }
-            rm &= rm - 1;
-        }
-        const unsigned nb = __ballot_sync(0xffffffffu, found);
-        if (lane == 0) {
-            f_next[w] = nb;
-            if (nb) p.P[w] = pw | nb;
-        }
-        if (found) {
-            depth[v] = level + 1;
-            if (parent) parent[v] = par;
-            ef += (unsigned long long)(p.symmetric ? (end - beg) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
-            cn += 1;
-        }
-    }
-    ef = warp_sum(ef);
-    cn = warp_sum(cn);
-    if (lane == 0) {
+    pull_level_words<true>(p, L, f_cur, f_next);
+    unsigned long long ef = warp_sum(L.ef);
+    unsigned long long cn = warp_sum(L.cnt);
+    if (lane_id() == 0) {
         s_ef[threadIdx.x >> 5] = ef;
         s_cn[threadIdx.x >> 5] = cn;
     }

@@ -68,7 +68,6 @@ void free_ws1(Workspace1* w) {
 template <int T>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
-    __shared__ PullSmem s_pull[T / 32];
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
     Ctl1* ctl = p.ctl;
@@ -186,7 +185,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.qbuf = sm.qbuf + warp * QBUF;
         L.qn = 0;
         if (dir == BFS_DIR_PULL) {
-            pull_level(p, L, f_cur, f_nxt, s_pull[warp]);
+            pull_level_words<false>(p, L, f_cur, f_nxt);
         } else {
             push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
         }
@@ -340,15 +339,10 @@ bfs_status sync_graph(bfs_graph* g, cudaStream_t st) {
 
 static float flog2(double x) { return (float)std::log2(x); }
 
-// Runs one source (already validated).  Returns after enqueueing unless a
-// host readback is needed (host loop, level log, level count); device-side
-// failures of asynchronous runs are reported by sync_graph / bfs_sync.
-bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* parent, const bfs_options& o,
-                      const float* mlp_dev, cudaStream_t st) {
-    Workspace1* w;
-    bfs_status s = ensure_ws1(g, o.chunk, st, &w);
-    if (s != BFS_OK) return s;
-    Params1 p{};
+// Kernel parameters of one single-source run (workspace, graph, options).
+static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o, const float* mlp_dev, int32_t src_value,
+                              int32_t* depth, int32_t* parent, cudaStream_t st, Params1& p) {
+    p = Params1{};
     p.n = g->n;
     p.W = w->W;
     p.m = g->m;
@@ -372,6 +366,7 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
     p.depth = depth;
     p.parent = parent;
     p.policy = o.policy;
+    p.force_dir = -1;
     p.alpha = o.alpha;
     p.beta = o.beta;
     p.gamma = o.gamma;
@@ -408,22 +403,43 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
         p.log = w->d_log;
         p.log_cap = o.level_log_cap;
     }
-    if (o.mode == BFS_MODE_GRAPH) return run_graph_mode(g, w, p, src_value, depth, parent, o, st);
-    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
-    int T = o.block_threads;
-    int blocks = 0;
-    switch (T) {
-        case 256: blocks = max_coop_blocks<256>(o.blocks_per_sm); break;
-        case 1024: blocks = max_coop_blocks<1024>(o.blocks_per_sm); break;
-        default: T = 512; blocks = max_coop_blocks<512>(o.blocks_per_sm); break;
+    return BFS_OK;
+}
+
+struct CoopLauncher {
+    int T = 512, blocks = 0;
+    explicit CoopLauncher(const bfs_options& o) {
+        T = o.block_threads;
+        switch (T) {
+            case 256: blocks = max_coop_blocks<256>(o.blocks_per_sm); break;
+            case 1024: blocks = max_coop_blocks<1024>(o.blocks_per_sm); break;
+            default: T = 512; blocks = max_coop_blocks<512>(o.blocks_per_sm); break;
+        }
     }
-    auto launch = [&](const Params1& pp) -> cudaError_t {
+    cudaError_t operator()(const Params1& pp, cudaStream_t st) const {
         switch (T) {
             case 256: return launch_bfs1<256>(pp, blocks, st);
             case 1024: return launch_bfs1<1024>(pp, blocks, st);
             default: return launch_bfs1<512>(pp, blocks, st);
         }
-    };
+    }
+};
+
+// Runs one source (already validated).  Returns after enqueueing unless a
+// host readback is needed (host loop, level log, level count); device-side
+// failures of asynchronous runs are reported by sync_graph / bfs_sync.
+bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* parent, const bfs_options& o,
+                      const float* mlp_dev, cudaStream_t st) {
+    Workspace1* w;
+    bfs_status s = ensure_ws1(g, o.chunk, st, &w);
+    if (s != BFS_OK) return s;
+    Params1 p;
+    s = make_params(g, w, o, mlp_dev, src_value, depth, parent, st, p);
+    if (s != BFS_OK) return s;
+    if (o.mode == BFS_MODE_GRAPH) return run_graph_mode(g, w, p, src_value, depth, parent, o, st);
+    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
+    CoopLauncher launcher(o);
+    auto launch = [&](const Params1& pp) -> cudaError_t { return launcher(pp, st); };
     if (o.mode == BFS_MODE_HOST_LOOP) {
         p.do_init = 1;
         p.level_count = 0;
@@ -459,3 +475,117 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
 }
 
 }  // namespace bfsgb
+
+// ------------------------------------------------------------ level profiling
+using namespace bfsgb;
+
+// Per-level timings of the three traversal forms from identical states: the
+// training signal of the learned direction policy.  See bfs.h.
+extern "C" bfs_status bfs_profile_levels(const bfs_graph* gc, int32_t source, const bfs_options* opt, int32_t repeats,
+                                         int32_t max_levels, float* features, float* times_us, int32_t* taken,
+                                         int32_t* levels, void* cuda_stream) {
+    bfs_graph* g = const_cast<bfs_graph*>(gc);
+    if (!g || !features || !times_us || !levels) return fail(BFS_EINVAL, "null argument");
+    if (source < 0 || source >= g->n) return fail(BFS_EINVAL, "source %d outside [0, %d)", source, g->n);
+    if (repeats < 1 || max_levels < 1) return fail(BFS_EINVAL, "repeats and max_levels must be >= 1");
+    bfs_options o;
+    bfs_options_init(&o);
+    if (opt) {
+        if (opt->struct_size != sizeof(bfs_options)) return fail(BFS_EINVAL, "bfs_options.struct_size mismatch");
+        o = *opt;
+    }
+    if (o.policy == BFS_POLICY_MLP || o.policy == BFS_POLICY_SCHEDULE) o.policy = BFS_POLICY_HEURISTIC;
+    o.level_log = nullptr;
+    o.levels_out = nullptr;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::lock_guard<std::mutex> lk(g->lock);
+    Workspace1* w;
+    bfs_status s = ensure_ws1(g, o.chunk, st, &w);
+    if (s != BFS_OK) return s;
+    if (!w->stage_depth) {
+        if (cudaMalloc(&w->stage_depth, (size_t)g->n * 4) != cudaSuccess ||
+            cudaMalloc(&w->stage_parent, (size_t)g->n * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BFS_ENOMEM, "profiling outputs");
+        }
+    }
+    Params1 p;
+    s = make_params(g, w, o, nullptr, source, w->stage_depth, w->stage_parent, st, p);
+    if (s != BFS_OK) return s;
+    uint32_t *snapP = nullptr, *snapF = nullptr;
+    Ctl1* snapC = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(snapP);
+        cudaFree(snapF);
+        cudaFree(snapC);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&snapP, w->W * 4) != cudaSuccess || cudaMalloc(&snapF, w->W * 4) != cudaSuccess ||
+        cudaMalloc(&snapC, sizeof(Ctl1)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(BFS_ENOMEM, "profiling snapshot");
+    }
+    CoopLauncher launch(o);
+    cudaError_t e = cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st);
+    p.do_init = 1;
+    p.level_count = 0;
+    if (!e) e = launch(p, st);
+    p.do_init = 0;
+    p.level_count = 1;
+    int L = 0;
+    std::vector<float> samples(repeats);
+    while (!e && L < max_levels) {
+        e = cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl1), cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaStreamSynchronize(st);
+        if (e) break;
+        Ctl1 h = *w->h_ctl;
+        if (h.bar.err) {
+            cleanup();
+            return device_error(h.bar.err, o.barrier_timeout_ns);
+        }
+        const Counters& c = h.slot[L % 3];
+        if (h.done || c.q_len == 0) break;
+        long long m_u = L > 0 ? h.m_u - (long long)c.e_f : h.m_u;
+        policy_features(features + (size_t)L * BFS_MLP_IN, (long long)c.q_len, (long long)c.e_f, m_u, L, h.prev_dir,
+                        g->n, p.log_n, p.log_m, p.log_degmax);
+        uint32_t* f_cur = (L & 1) ? w->F[1] : w->F[0];
+        e = cudaMemcpyAsync(snapP, w->P, w->W * 4, cudaMemcpyDeviceToDevice, st);
+        if (!e) e = cudaMemcpyAsync(snapF, f_cur, w->W * 4, cudaMemcpyDeviceToDevice, st);
+        if (!e) e = cudaMemcpyAsync(snapC, w->ctl, sizeof(Ctl1), cudaMemcpyDeviceToDevice, st);
+        for (int d = 0; d < 3 && !e; ++d) {
+            Params1 q = p;
+            q.force_dir = d;
+            for (int r = 0; r < repeats && !e; ++r) {
+                e = cudaMemcpyAsync(w->P, snapP, w->W * 4, cudaMemcpyDeviceToDevice, st);
+                if (!e) e = cudaMemcpyAsync(f_cur, snapF, w->W * 4, cudaMemcpyDeviceToDevice, st);
+                if (!e) e = cudaMemcpyAsync(w->ctl, snapC, sizeof(Ctl1), cudaMemcpyDeviceToDevice, st);
+                if (!e) e = cudaEventRecord(e0, st);
+                if (!e) e = launch(q, st);
+                if (!e) e = cudaEventRecord(e1, st);
+                if (!e) e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+                samples[r] = ms * 1000.0f;
+            }
+            std::sort(samples.begin(), samples.end());
+            times_us[(size_t)L * 3 + d] = samples[repeats / 2];
+        }
+        // continue with the plain method's own choice from the same state
+        if (!e) e = cudaMemcpyAsync(w->P, snapP, w->W * 4, cudaMemcpyDeviceToDevice, st);
+        if (!e) e = cudaMemcpyAsync(f_cur, snapF, w->W * 4, cudaMemcpyDeviceToDevice, st);
+        if (!e) e = cudaMemcpyAsync(w->ctl, snapC, sizeof(Ctl1), cudaMemcpyDeviceToDevice, st);
+        if (!e) e = launch(p, st);
+        if (!e) e = cudaMemcpyAsync(w->h_ctl, w->ctl, sizeof(Ctl1), cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaStreamSynchronize(st);
+        if (!e && taken) taken[L] = w->h_ctl->prev_dir;
+        ++L;
+    }
+    cleanup();
+    if (e) return cuda_fail(e, "level profiling");
+    *levels = L;
+    return BFS_OK;
+}

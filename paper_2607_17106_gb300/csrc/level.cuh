@@ -87,6 +87,7 @@ struct Params1 {
     int32_t* parent;
     // policy
     int32_t policy;
+    int32_t force_dir;  // >= 0: every level uses this form (level profiling)
     float alpha, beta, gamma;
     const int8_t* schedule;
     int32_t schedule_len;
@@ -111,6 +112,7 @@ __device__ __forceinline__ int push_kind(const Params1& p, long long f) {
 // Same inputs on every CTA -> same decision (all arithmetic is deterministic).
 __device__ inline int decide_dir(const Params1& p, int level, long long f, long long e_f, long long m_u, long long f_prev,
                           int prev_dir, float* s_feat, float* s_mlp_out) {
+    if (p.force_dir >= 0) return p.force_dir;
     switch (p.policy) {
         case BFS_POLICY_PUSH:
             return push_kind(p, f);
@@ -149,6 +151,12 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
         }
     }
 }
+
+// Loads of P and of the frontier bitmaps are ordinary (L1-cacheable) loads:
+// the writes of the previous level are ordered before them by the grid
+// barrier's acquire (or by the kernel boundary in graph mode), and within a
+// level P only gains bits, so a stale word can only cost an extra OR.  Hub
+// rows make a few frontier words very hot, which the L1 then serves.
 
 // ------------------------------------------------------------ claiming
 constexpr int QBUF = 64;  // per-warp shared-memory staging of next-queue entries
@@ -214,7 +222,7 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
     if (has) {
         w = (unsigned)v >> 5;
         bit = 1u << (v & 31);
-        want = !(__ldcg(p.P + w) & bit);
+        want = !(p.P[w] & bit);  // may be stale (bits only grow): the OR decides
     }
     bool claimed = false;
     if (p.aggregate) {
@@ -343,7 +351,7 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
             } else {
                 long long w = t * (T / 32) + (threadIdx.x >> 5);
                 if (w < p.W) {
-                    unsigned fw = __ldcg(f_cur + w);
+                    unsigned fw = f_cur[w];
                     if ((fw >> (threadIdx.x & 31)) & 1u) u = (int)(w * 32 + (threadIdx.x & 31));
                 }
             }
@@ -354,194 +362,92 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
 }
 
 // ------------------------------------------------------------ pull level
-constexpr int PULL_ILP = 8;     // words a warp handles per step
-constexpr int PULL_BLOCK = 16;  // words of P a warp reads per block
-constexpr int PULL_LIST = 32 * PULL_ILP;  // leftover rows of one step (at most every row)
+constexpr int PULL_SERIAL_MAX = 32;  // row entries one lane scans before its warp takes over
 
-// Per-warp shared memory of the pull level.
-struct PullSmem {
-    int v[PULL_LIST];     // leftover row: vertex
-    int j[PULL_LIST];     //   next position to test
-    int end[PULL_LIST];   //   row end
-    int off[PULL_LIST + 1];
-    unsigned hit[PULL_LIST];  // lowest hit position of this round, ~0u if none
-    unsigned word_nb[PULL_ILP];  // found bits per word of the step
-};
-
-// One pull step over up to PULL_ILP 32-vertex words (lane = vertex of each
-// word).  Phase 1: every unvisited row tests its first in-neighbour, all
-// rows' loads in flight together.  Phase 2: rows not yet resolved go to a
-// shared-memory list that the warp scans flattened: each round every live row
-// contributes up to `pull_serial` entries, a prefix over the list lays the
-// entries out over the lanes, and the lowest hit position of a row (a min in
-// shared memory) gives its parent.  Phase 3 writes the words of P and F_{i+1}.
-__device__ __forceinline__ void pull_step(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                                          long long wb, const int (&wi)[PULL_ILP], const unsigned (&pwi)[PULL_ILP],
-                                          PullSmem& ps) {
-    const unsigned lane = lane_id();
-    const int dnext = L.level + 1;
-    int beg[PULL_ILP], end[PULL_ILP], u0[PULL_ILP];
-#pragma unroll
-    for (int k = 0; k < PULL_ILP; ++k) {
-        bool unvis = !((pwi[k] >> lane) & 1u);
-        long long v = (wb + wi[k]) * 32 + lane;
-        beg[k] = unvis ? __ldg(p.csc_ptr + v) : 0;
-        end[k] = unvis ? __ldg(p.csc_ptr + v + 1) : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < PULL_ILP; ++k) u0[k] = (beg[k] < end[k]) ? __ldg(p.csc_col + beg[k]) : -1;
-    int nlist = 0;
-#pragma unroll
-    for (int k = 0; k < PULL_ILP; ++k) {
-        bool found = u0[k] >= 0 && ((__ldcg(f_cur + (u0[k] >> 5)) >> (u0[k] & 31)) & 1u);
-        long long v = (wb + wi[k]) * 32 + lane;
-        if (found) {
-            L.depth[v] = dnext;
-            if (L.parent) L.parent[v] = u0[k];
-            int dg = p.symmetric ? end[k] - beg[k] : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
-            L.ef += (unsigned long long)dg;
-            L.cnt += 1;
-        }
-        unsigned nb = __ballot_sync(0xffffffffu, found);
-        if (lane == 0) ps.word_nb[k] = nb;
-        bool left = u0[k] >= 0 && !found && beg[k] + 1 < end[k];
-        unsigned lm = __ballot_sync(0xffffffffu, left);
-        if (left) {
-            int r = nlist + __popc(lm & lanemask_lt());
-            ps.v[r] = (int)v;
-            ps.j[r] = beg[k] + 1;
-            ps.end[r] = end[k];
-        }
-        nlist += __popc(lm);
-    }
-    __syncwarp();
-    const int cap = p.pull_serial;
-    while (nlist > 0) {
-        // contributions and their prefix (rows lane, lane+32, ...)
-        int loc = 0;
-        for (int r = (int)lane; r < nlist; r += 32) loc += min(ps.end[r] - ps.j[r], cap);
-        int incl = loc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        // per-lane rows are strided, so lay offsets out row by row
-        // (prefix in row order = sum over earlier rows): recompute serially
-        // per lane group of 32 rows
-        int run = 0;
-        for (int r0 = 0; r0 < nlist; r0 += 32) {
-            int r = r0 + (int)lane;
-            int c = r < nlist ? min(ps.end[r] - ps.j[r], cap) : 0;
-            int ci = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, ci, o);
-                if ((int)lane >= o) ci += y;
-            }
-            if (r < nlist) {
-                ps.off[r] = run + ci - c;
-                ps.hit[r] = ~0u;
-            }
-            run += __shfl_sync(0xffffffffu, ci, 31);
-        }
-        if (lane == 0) ps.off[nlist] = total;
-        __syncwarp();
-        for (int e0 = 0; e0 < total; e0 += 32) {
-            int x = e0 + (int)lane;
-            if (x < total) {
-                int lo = 0, hi = nlist - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (ps.off[mid] <= x) lo = mid; else hi = mid - 1;
-                }
-                int pos = ps.j[lo] + (x - ps.off[lo]);
-                int u = __ldg(p.csc_col + pos);
-                if ((__ldcg(f_cur + (u >> 5)) >> (u & 31)) & 1u) atomicMin(&ps.hit[lo], (unsigned)pos);
-            }
-        }
-        __syncwarp();
-        // resolve rows; keep the live ones (compacted) for the next round
-        int keep = 0;
-        for (int r0 = 0; r0 < nlist; r0 += 32) {
-            int r = r0 + (int)lane;
-            bool live = false;
-            int rv = 0, rj = 0, re = 0;
-            if (r < nlist) {
-                rv = ps.v[r];
-                rj = ps.j[r];
-                re = ps.end[r];
-                unsigned h = ps.hit[r];
-                if (h != ~0u) {
-                    int par = __ldg(p.csc_col + h);
-                    L.depth[rv] = dnext;
-                    if (L.parent) L.parent[rv] = par;
-                    int dg = p.symmetric ? (__ldg(p.csc_ptr + rv + 1) - __ldg(p.csc_ptr + rv))
-                                         : (__ldg(p.row_ptr + rv + 1) - __ldg(p.row_ptr + rv));
-                    L.ef += (unsigned long long)dg;
-                    L.cnt += 1;
-                    long long w = rv >> 5;
-                    // the word's index within the step
-#pragma unroll
-                    for (int k = 0; k < PULL_ILP; ++k)
-                        if (wi[k] >= 0 && wb + wi[k] == w) atomicOr(&ps.word_nb[k], 1u << (rv & 31));
-                } else {
-                    rj += min(re - rj, cap);
-                    live = rj < re;
-                }
-            }
-            unsigned lm = __ballot_sync(0xffffffffu, live);
-            __syncwarp();
-            if (live) {
-                int q = keep + __popc(lm & lanemask_lt());
-                ps.v[q] = rv;
-                ps.j[q] = rj;
-                ps.end[q] = re;
-            }
-            keep += __popc(lm);
-            __syncwarp();
-        }
-        nlist = keep;
-    }
-    __syncwarp();
-    if ((int)lane < PULL_ILP && wi[lane] >= 0) {
-        long long w = wb + wi[lane];
-        unsigned nb = ps.word_nb[lane];
-        f_next[w] = nb;
-        if (nb) p.P[w] = pwi[lane] | nb;
-    }
-    __syncwarp();
+template <bool NC>
+__device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
+    return NC ? __ldg(a + i) : a[i];
 }
 
-// Pull level: each warp reads PULL_BLOCK words of P with one coalesced load,
-// writes F_{i+1} = 0 for the fully visited ones, and handles the others
-// PULL_ILP at a time.
-__device__ inline void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next, PullSmem& ps) {
-    unsigned lane = lane_id();
-    long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long wb = gwarp * PULL_BLOCK; wb < p.W; wb += nwarps * PULL_BLOCK) {
-        long long wl = wb + lane;
-        bool mine = lane < PULL_BLOCK && wl < p.W;
-        unsigned pw = mine ? __ldcg(p.P + wl) : 0xffffffffu;
-        if (mine && pw == 0xffffffffu) f_next[wl] = 0;
-        unsigned todo = __ballot_sync(0xffffffffu, pw != 0xffffffffu);
-        while (todo) {
-            int wi[PULL_ILP];
-            unsigned pwi[PULL_ILP];
-#pragma unroll
-            for (int k = 0; k < PULL_ILP; ++k) {
-                if (todo) {
-                    wi[k] = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    pwi[k] = __shfl_sync(0xffffffffu, pw, wi[k]);
-                } else {
-                    wi[k] = -1;
-                    pwi[k] = 0xffffffffu;
+// Pull level (Section 5, loop order d -> s): one warp per 32-vertex word of P
+// (lane = vertex), words dealt round-robin over all warps of the grid.  An
+// unvisited lane scans its in-neighbours in ascending order and stops at the
+// first one in F_i (ANY = the lowest-index frontier neighbour); rows longer
+// than `pull_serial` entries are finished by the whole warp 32 entries at a
+// time.  The warp writes the word of P and of F_{i+1} with plain stores (it
+// owns the word) and counts |F_{i+1}| and e_f in registers.  NC selects
+// non-coherent loads of P and F_i, valid when no other CTA writes them during
+// the kernel (the graph-mode kernel); the persistent kernel uses ordinary
+// loads ordered by its grid barrier.
+template <bool NC>
+__device__ __forceinline__ void pull_level_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
+                                                 uint32_t* f_next) {
+    const unsigned lane = lane_id();
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int dnext = L.level + 1;
+    const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.W; w += nwarps) {
+        const unsigned pw = ld_word<NC>(p.P, w);
+        if (pw == 0xffffffffu) {
+            if (lane == 0) f_next[w] = 0;
+            continue;
+        }
+        const long long v = w * 32 + lane;
+        const bool unvis = !((pw >> lane) & 1u);
+        int beg = 0, end = 0;
+        if (unvis) {
+            beg = __ldg(p.csc_ptr + v);
+            end = __ldg(p.csc_ptr + v + 1);
+        }
+        bool found = false;
+        int par = -1;
+        int j = beg;
+        const int lim = min(end, beg + serial);
+        for (; j < lim; ++j) {
+            const int u = __ldg(p.csc_col + j);
+            if ((ld_word<NC>(f_cur, u >> 5) >> (u & 31)) & 1u) {
+                found = true;
+                par = u;
+                break;
+            }
+        }
+        unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && j < end);
+        while (rm) {
+            const int l = __ffs(rm) - 1;
+            const int bl = __shfl_sync(0xffffffffu, j, l);
+            const int el = __shfl_sync(0xffffffffu, end, l);
+            int hit = -1;
+            for (int base = bl; base < el; base += 32) {
+                const int idx = base + (int)lane;
+                int uu = 0;
+                bool h = false;
+                if (idx < el) {
+                    uu = __ldg(p.csc_col + idx);
+                    h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+                }
+                const unsigned hb = __ballot_sync(0xffffffffu, h);
+                if (hb) {
+                    hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
+                    break;
                 }
             }
-            pull_step(p, L, f_cur, f_next, wb, wi, pwi, ps);
+            if ((int)lane == l && hit >= 0) {
+                found = true;
+                par = hit;
+            }
+            rm &= rm - 1;
+        }
+        const unsigned nb = __ballot_sync(0xffffffffu, found);
+        if (lane == 0) {
+            f_next[w] = nb;
+            if (nb) p.P[w] = pw | nb;
+        }
+        if (found) {
+            L.depth[v] = dnext;
+            if (L.parent) L.parent[v] = par;
+            L.ef += (unsigned long long)(p.symmetric ? (end - beg)
+                                                     : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+            L.cnt += 1;
         }
     }
 }

@@ -99,3 +99,54 @@ def test_training_reduces_loss_on_a_separable_task():
     pol.forward(Xd, out, rows)
     acc = (out.argmax(1).cpu().numpy() == y).mean()
     assert acc > 0.9
+
+
+def test_profile_levels_records_every_level_of_the_plain_method():
+    import graphgen
+    n, s, d = graphgen.rmat(14, 16, seed=1)
+    adj = oracle.build_adjacency(n, s, d)
+    g = bg.Graph.build(n, s, d)
+    src = int(graphgen.sample_sources(n, s, d, 1, seed=3)[0])
+    X, T, taken = g.profile_levels(src, repeats=3)
+    ref_depth, _ = oracle.bfs(adj, src)
+    st = oracle.level_stats(adj, ref_depth)
+    assert len(X) == len(st)
+    assert np.all(T > 0) and np.all((taken >= 0) & (taken <= 2))
+    m_u = adj.m - st[0][1]
+    for i in range(len(st)):
+        f, e_f = st[i][0], st[i][1]
+        if i > 0:
+            m_u -= e_f
+        ref = g.features(i, f, e_f, m_u, taken[i - 1] if i > 0 else bg.BFS_DIR_PUSH_QUEUE)
+        assert np.allclose(X[i], ref), (i, X[i], ref)
+    # the profiled search left a correct search behind: a normal run still matches
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.run(np.array([src], np.int32), depth, None, bg.options(batch=0))
+    g.sync()
+    assert np.array_equal(depth.cpu().numpy(), ref_depth)
+
+
+def test_policy_pipeline_trains_and_drives_searches():
+    from paper_2607_17106_gb300 import policy as pl
+    specs = pl.training_specs(6, 12, 14, seed=77)
+    X, T, K, G = pl.collect(specs, sources_per_graph=2, repeats=1)
+    y = T.argmin(axis=1).astype(np.int32)
+    pol = pl.fit(X, y, epochs=300, lr=3e-3)
+    assert np.isfinite(pol.final_loss)
+    choice = pl.predict(pol, X)
+    assert choice.shape == y.shape
+    import graphgen
+    n, s, d = graphgen.rmat(13, 16, seed=5)
+    adj = oracle.build_adjacency(n, s, d)
+    g = bg.Graph.build(n, s, d)
+    srcs = graphgen.sample_sources(n, s, d, 8, seed=9)
+    depth = torch.empty((8, n), dtype=torch.int32, device="cuda")
+    parent = torch.empty((8, n), dtype=torch.int32, device="cuda")
+    for batch in (0, 1):
+        g.run(srcs, depth, parent, bg.options(batch=batch, policy=bg.BFS_POLICY_MLP, mlp=pol))
+        g.sync()
+        dh, ph = depth.cpu().numpy(), parent.cpu().numpy()
+        for j, src in enumerate(srcs):
+            ref, _ = oracle.bfs(adj, int(src))
+            assert np.array_equal(dh[j], ref)
+            assert oracle.validate(adj, int(src), dh[j], ph[j]) == 0
