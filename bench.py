@@ -130,6 +130,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def source_hash() -> str:
+    """Hash of the CUDA sources: a recorded ncu traffic figure is only valid for this code."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_17106_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the BFS kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
 def measured_peak():
     try:
         with open(PEAKS_FILE) as f:
@@ -282,7 +307,7 @@ def main():
     roof = {"bound": "hbm", "kernel": "bfs1_kernel (persistent level loop)", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS, "bytes_per_launch": mean_bmin,
-            "launch_us": mean_launch_s * 1e6, "traffic": None}
+            "launch_us": mean_launch_s * 1e6, "traffic": recorded_traffic(w.name)}
 
     extra = {}
     if not args.no_extra:

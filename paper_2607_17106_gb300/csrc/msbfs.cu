@@ -47,7 +47,8 @@ struct CountersMS {
     unsigned long long a_len;  // active vertices appended (front != 0)
     unsigned long long u_len;  // chunk units appended
     unsigned long long e_f;    // degree sum of the appended vertices
-    unsigned long long work;   // work counter of the level that fills this slot
+    unsigned long long conv;   // cursor of a masks -> active-list conversion
+    unsigned long long lanes;  // OR of the frontier masks: lanes that can still find vertices
 };
 
 struct CtlMS {
@@ -136,18 +137,22 @@ struct UnitView {
     uint64_t lanes;
 };
 
+constexpr int MS_T = 512;
+constexpr int MS_QBUF = 64;  // per-warp staging of active-list appends
+
 struct MsSmem {
     int32_t* depth[64];
     int32_t* parent[64];
-    int off[513];
-    int beg[512];
-    int src[512];
-    unsigned long long fmask[512];
+    int off[MS_T + 1];
+    int beg[MS_T];
+    int src[MS_T];
+    unsigned long long fmask[MS_T];
     int scan_tmp[33];
-    int item;
+    int32_t qbuf[(MS_T / 32) * MS_QBUF];
     float feat[BFS_MLP_IN];
     float mlp_out;
-    unsigned long long red[16];
+    unsigned long long red[MS_T / 32];
+    unsigned long long base;
 };
 
 struct MsLevel {
@@ -156,7 +161,12 @@ struct MsLevel {
     int32_t* a_next;
     int2* u_next;
     CountersMS* next;
-    unsigned long long ef;
+    unsigned long long ef;   // degree sum of F_{i+1} vertices (this thread's share)
+    unsigned long long cnt;  // |{v : F_{i+1}[v] != 0}| (pull levels, this thread's share)
+    uint64_t lanes;          // OR of the F_{i+1} masks this thread wrote
+    uint64_t live;           // lanes with a non-empty frontier F_i
+    int32_t* qbuf;
+    int qn;                  // staged appends (warp-uniform)
 };
 
 __device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, int par, int d) {
@@ -168,56 +178,74 @@ __device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, in
     }
 }
 
-// v became active in F_{i+1} (first touch): append to the active list,
-// degree sum, chunk units for big rows.  Warp-uniform.
-__device__ __forceinline__ void ms_emit(const ParamsMS& p, const UnitView& g, MsLevel& L, bool first, int v, int deg) {
-    unsigned cm = __ballot_sync(0xffffffffu, first);
-    if (!cm) return;
-    int leader = __ffs(cm) - 1;
-    unsigned long long base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(&L.next->a_len, (unsigned long long)__popc(cm));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (first) {
-        L.a_next[base + __popc(cm & lanemask_lt())] = v;
-        L.ef += (unsigned long long)deg;
-        if (deg >= p.chunk) {
-            int nch = (deg + p.chunk - 1) / p.chunk;
-            unsigned long long ub = atomicAdd(&L.next->u_len, (unsigned long long)nch);
-            if (ub + nch <= (unsigned long long)p.ucap) {
-                for (int c = 0; c < nch; ++c) L.u_next[ub + c] = make_int2(v, c);
-            } else {
-                atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-            }
-        }
+__device__ __forceinline__ void ms_units(const ParamsMS& p, int2* u_out, CountersMS* c, int v, int deg) {
+    int nch = (deg + p.chunk - 1) / p.chunk;
+    unsigned long long ub = atomicAdd(&c->u_len, (unsigned long long)nch);
+    if (ub + nch <= (unsigned long long)p.ucap) {
+        for (int k = 0; k < nch; ++k) u_out[ub + k] = make_int2(v, k);
+    } else {
+        atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
     }
 }
 
+__device__ __forceinline__ void ms_flush(MsLevel& L) {
+    if (L.qn == 0) return;
+    unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&L.next->a_len, (unsigned long long)L.qn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    for (int i = (int)lane; i < L.qn; i += 32) L.a_next[base + i] = L.qbuf[i];
+    __syncwarp();
+    L.qn = 0;
+}
+
+// v entered F_{i+1} (first OR into its mask this level): stage it for the
+// active list, add its degree, split big rows into chunk units.  Warp-uniform.
+__device__ __forceinline__ void ms_emit(const ParamsMS& p, MsLevel& L, bool first, int v, int deg) {
+    unsigned cm = __ballot_sync(0xffffffffu, first);
+    if (!cm) return;
+    int c = __popc(cm);
+    if (L.qn + c > MS_QBUF) ms_flush(L);
+    if (first) {
+        L.qbuf[L.qn + __popc(cm & lanemask_lt())] = v;
+        L.ef += (unsigned long long)deg;
+        if (deg >= p.chunk) ms_units(p, L.u_next, L.next, v, deg);
+    }
+    L.qn += c;
+}
+
+// Push candidate u -> v with frontier lanes fu: the lanes of fu that v has
+// not seen are ORed into next[v]; the OR's old value names exactly one
+// claimer per (v, lane), which writes that lane's depth and parent.
 __device__ __forceinline__ void ms_candidate(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, bool has,
                                              int v, int u, uint64_t fu) {
     uint64_t bits = 0;
-    if (has) bits = fu & ~__ldcg((const unsigned long long*)p.seen + v);
+    if (has) bits = fu & ~((const unsigned long long*)p.seen)[v];
     bool first = false;
     int deg = 0;
     if (bits) {
         uint64_t old = atomicOr((unsigned long long*)L.f_next + v, (unsigned long long)bits);
         uint64_t nb = bits & ~old;
         first = (old == 0);
+        L.lanes |= nb;
         if (nb) write_lanes(sm, nb, v, u, L.level + 1);
         if (first) deg = __ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v);
     }
-    ms_emit(p, g, L, first, v, deg);
+    ms_emit(p, L, first, v, deg);
 }
 
 template <int T>
-__device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, int u) {
+__device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, int u,
+                             const uint64_t* f_cur) {
     unsigned lane = lane_id();
     int beg = 0, end = 0;
     uint64_t fu = 0;
     if (u >= 0) {
         beg = __ldg(g.row_ptr + u);
         end = __ldg(g.row_ptr + u + 1);
-        fu = __ldcg((const unsigned long long*)(((L.level & 1) ? p.F1 : p.F0)) + u);
-        if (end - beg >= p.chunk) end = beg;
+        fu = ((const unsigned long long*)f_cur)[u];
+        if (end - beg >= p.chunk) end = beg;  // chunk units cover it
     }
     bool med = (end - beg) >= p.medium;
     unsigned mm = __ballot_sync(0xffffffffu, med);
@@ -264,21 +292,17 @@ __device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, M
     __syncthreads();
 }
 
+// Push level: items = chunk units of big rows, then CTA tiles of the active
+// list, dealt round-robin over the CTAs.
 template <int T>
 __device__ void ms_push_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const int32_t* a_cur,
-                              const int2* u_cur, const uint64_t* f_cur, long long a, long long nunits, CountersMS* work) {
-    long long ntiles = (a + T - 1) / T;
-    long long nitems = nunits + ntiles;
-    while (true) {
-        if (threadIdx.x == 0) sm.item = (int)atomicAdd(&work->work, 1ull);
-        __syncthreads();
-        long long it = sm.item;
-        __syncthreads();
-        if (it >= nitems) break;
+                              const int2* u_cur, const uint64_t* f_cur, long long a, long long nunits) {
+    long long nitems = nunits + (a + T - 1) / T;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
         if (it < nunits) {
-            int2 un = __ldcg(u_cur + it);
+            int2 un = u_cur[it];
             int u = un.x;
-            uint64_t fu = __ldcg((const unsigned long long*)f_cur + u);
+            uint64_t fu = ((const unsigned long long*)f_cur)[u];
             int b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
             int lo = b + un.y * p.chunk, hi = min(e, lo + p.chunk);
             for (int base = lo; base < hi; base += T) {
@@ -289,10 +313,11 @@ __device__ void ms_push_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             }
         } else {
             long long q = (it - nunits) * T + threadIdx.x;
-            int u = q < a ? __ldcg(a_cur + q) : -1;
-            ms_push_tile<T>(p, g, L, sm, u);
+            int u = q < a ? a_cur[q] : -1;
+            ms_push_tile<T>(p, g, L, sm, u, f_cur);
         }
     }
+    ms_flush(L);
 }
 
 __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
@@ -301,17 +326,26 @@ __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
     return ((uint64_t)hi << 32) | lo;
 }
 
+// Pull level, one warp per 32 consecutive vertices (lane = vertex): a vertex
+// missing some live lanes (lanes whose frontier F_i is not empty: only those
+// can reach it at this level) ORs the frontier masks of its in-neighbours in
+// ascending order and stops once every such lane is found; the first
+// neighbour that supplies a lane is that lane's parent.  Rows longer than
+// `pull_serial` entries are finished by the whole warp.  Depths are written
+// lane-major in a warp-uniform loop over the union of the new lanes, so the
+// 32 vertices' entries of one lane's depth row go out together.
 __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const uint64_t* f_cur) {
-    unsigned lane = lane_id();
-    long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = lane_id();
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int dnext = L.level + 1;
-    for (long long base = gwarp * 32; base < g.n; base += nwarps * 32) {
-        long long v = base + lane;
+    const long long W = (g.n + 31) >> 5;
+    const unsigned long long* F = (const unsigned long long*)f_cur;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < W; w += nwarps) {
+        const long long v = w * 32 + lane;
         uint64_t miss = 0;
         if (v < g.n) {
-            bool iso = (__ldg(g.isolated + (v >> 5)) >> (v & 31)) & 1u;
-            if (!iso) miss = g.lanes & ~__ldcg((const unsigned long long*)p.seen + v);
+            bool iso = (__ldg(g.isolated + w) >> lane) & 1u;
+            if (!iso) miss = L.live & ~((const unsigned long long*)p.seen)[v];
         }
         if (!__ballot_sync(0xffffffffu, miss != 0)) continue;
         int beg = 0, end = 0;
@@ -321,41 +355,43 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
         }
         uint64_t acc = 0;
         int j = beg;
-        int lim = min(end, beg + p.pull_serial);
+        const int lim = min(end, beg + p.pull_serial);
         for (; j < lim && acc != miss; ++j) {
-            int u = __ldg(g.csc_col + j);
-            uint64_t got = __ldcg((const unsigned long long*)f_cur + u) & miss & ~acc;
+            const int u = __ldg(g.csc_col + j);
+            const uint64_t got = F[u] & miss & ~acc;
             if (got) {
                 acc |= got;
-                write_lanes(sm, got, (int)v, u, dnext);
+                uint64_t b = got;
+                while (b) {
+                    int lj = __ffsll((long long)b) - 1;
+                    if (sm.parent[lj]) sm.parent[lj][v] = u;
+                    b &= b - 1;
+                }
             }
         }
         unsigned rm = __ballot_sync(0xffffffffu, miss != 0 && acc != miss && j < end);
         while (rm) {
-            int l = __ffs(rm) - 1;
-            int jl = __shfl_sync(0xffffffffu, j, l);
-            int el = __shfl_sync(0xffffffffu, end, l);
-            uint64_t ml = __shfl_sync(0xffffffffu, (unsigned long long)miss, l);
+            const int l = __ffs(rm) - 1;
+            const int jl = __shfl_sync(0xffffffffu, j, l);
+            const int el = __shfl_sync(0xffffffffu, end, l);
+            const uint64_t ml = __shfl_sync(0xffffffffu, (unsigned long long)miss, l);
             uint64_t al = __shfl_sync(0xffffffffu, (unsigned long long)acc, l);
-            int vl = (int)(base + l);
+            const int vl = (int)(w * 32 + l);
             for (int b2 = jl; b2 < el && al != ml; b2 += 32) {
-                int idx = b2 + (int)lane;
+                const int idx = b2 + (int)lane;
                 int uu = 0;
                 uint64_t fu = 0;
                 if (idx < el) {
                     uu = __ldg(g.csc_col + idx);
-                    fu = __ldcg((const unsigned long long*)f_cur + uu) & ml & ~al;
+                    fu = F[uu] & ml & ~al;
                 }
-                uint64_t got = warp_or64(fu);
+                const uint64_t got = warp_or64(fu);
                 uint64_t gb = got;
                 while (gb) {  // warp-uniform: the first (lowest index) provider of each lane
-                    int bj = __ffsll((long long)gb) - 1;
-                    unsigned who = __ballot_sync(0xffffffffu, (fu >> bj) & 1ull);
-                    int par = __shfl_sync(0xffffffffu, uu, __ffs(who) - 1);
-                    if (lane == 0) {
-                        sm.depth[bj][vl] = dnext;
-                        if (sm.parent[bj]) sm.parent[bj][vl] = par;
-                    }
+                    const int bj = __ffsll((long long)gb) - 1;
+                    const unsigned who = __ballot_sync(0xffffffffu, (fu >> bj) & 1ull);
+                    const int par = __shfl_sync(0xffffffffu, uu, __ffs(who) - 1);
+                    if (lane == 0 && sm.parent[bj]) sm.parent[bj][vl] = par;
                     gb &= gb - 1;
                 }
                 al |= got;
@@ -363,14 +399,39 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             if ((int)lane == l) acc = al;
             rm &= rm - 1;
         }
-        bool first = acc != 0;
-        int deg = 0;
-        if (first) {
+        uint64_t all = warp_or64(acc);
+        while (all) {  // warp-uniform
+            const int bj = __ffsll((long long)all) - 1;
+            if ((acc >> bj) & 1ull) sm.depth[bj][v] = dnext;
+            all &= all - 1;
+        }
+        if (acc) {
             ((unsigned long long*)L.f_next)[v] = acc;
             ((unsigned long long*)p.seen)[v] |= acc;
-            deg = g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
+            L.lanes |= acc;
+            L.cnt += 1;
+            L.ef += (unsigned long long)(g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
         }
-        ms_emit(p, g, L, first, (int)v, deg);
+    }
+}
+
+// Active list of F_i from its masks (after a pull level), with chunk units.
+template <int T>
+__device__ void ms_masks_to_list(const ParamsMS& p, const UnitView& g, MsSmem& sm, const uint64_t* f_cur,
+                                 int32_t* a_cur, int2* u_cur, CountersMS* cur) {
+    for (long long vb = (long long)blockIdx.x * T; vb < g.n; vb += (long long)gridDim.x * T) {
+        long long v = vb + threadIdx.x;
+        int flag = (v < g.n && ((const unsigned long long*)f_cur)[v] != 0) ? 1 : 0;
+        int total;
+        int off = block_exclusive_scan(flag, sm.scan_tmp, &total);
+        if (threadIdx.x == 0 && total) sm.base = atomicAdd(&cur->conv, (unsigned long long)total);
+        __syncthreads();
+        if (flag) {
+            a_cur[sm.base + off] = (int)v;
+            int deg = __ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v);
+            if (deg >= p.chunk) ms_units(p, u_cur, cur, (int)v, deg);
+        }
+        __syncthreads();
     }
 }
 
@@ -416,6 +477,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
     const unsigned nblocks = gridDim.x;
     const long long gtid = (long long)blockIdx.x * T + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * T;
+    const unsigned warp = threadIdx.x >> 5;
     unsigned bar_target = 0;
     int total_levels = 0;
     for (int ui = 0; ui < p.n_units; ++ui) {
@@ -456,8 +518,10 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 ctl->slot[s].a_len = 0;
                 ctl->slot[s].u_len = 0;
                 ctl->slot[s].e_f = 0;
-                ctl->slot[s].work = 0;
+                ctl->slot[s].conv = 0;
+                ctl->slot[s].lanes = 0;
             }
+            ctl->slot[0].lanes = g.lanes;
         }
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         if (blockIdx.x == 0 && threadIdx.x < (unsigned)g.k) {
@@ -472,25 +536,19 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 unsigned long long idx = atomicAdd(&ctl->slot[0].a_len, 1ull);
                 p.A0[idx] = s;
                 atomicAdd(&ctl->slot[0].e_f, (unsigned long long)deg);
-                if (deg >= p.chunk) {
-                    int nch = (deg + p.chunk - 1) / p.chunk;
-                    unsigned long long ub = atomicAdd(&ctl->slot[0].u_len, (unsigned long long)nch);
-                    if (ub + nch <= (unsigned long long)p.ucap)
-                        for (int c = 0; c < nch; ++c) p.U0[ub + c] = make_int2(s, c);
-                    else
-                        atomicCAS(&ctl->bar.err, 0, (int)DEV_OVERFLOW);
-                }
+                if (deg >= p.chunk) ms_units(p, p.U0, &ctl->slot[0], s, deg);
             }
         }
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         long long m_u = g.m, a_prev = 0;
         int prev_dir = BFS_DIR_PUSH_QUEUE;
+        int list_valid = 0;  // level whose active list (and chunk units) exists
         for (int level = 0;; ++level) {
             CountersMS* cur = &ctl->slot[level % 3];
             CountersMS* nxt = &ctl->slot[(level + 1) % 3];
             long long a = (long long)__ldcg(&cur->a_len);
-            long long nunits = (long long)__ldcg(&cur->u_len);
             long long e_f = (long long)__ldcg(&cur->e_f);
+            const uint64_t live = (uint64_t)__ldcg(&cur->lanes);
             if (a == 0) break;
             if (level >= p.max_levels) {
                 if (gtid == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
@@ -508,16 +566,24 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 r.t_ns = (int64_t)globaltimer_ns();
                 p.log[level] = r;
             }
+            int32_t* a_cur = (level & 1) ? p.A1 : p.A0;
+            int2* u_cur = (level & 1) ? p.U1 : p.U0;
+            uint64_t* f_cur = (level & 1) ? p.F1 : p.F0;
+            if (dir != BFS_DIR_PULL && list_valid != level) {
+                // active list of a pull-made frontier
+                ms_masks_to_list<T>(p, g, sm, f_cur, a_cur, u_cur, cur);
+                if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+                list_valid = level;
+            }
+            long long nunits = (long long)__ldcg(&cur->u_len);
             if (gtid == 0) {
                 CountersMS* z = &ctl->slot[(level + 2) % 3];
                 z->a_len = 0;
                 z->u_len = 0;
                 z->e_f = 0;
-                z->work = 0;
+                z->conv = 0;
+                z->lanes = 0;
             }
-            const int32_t* a_cur = (level & 1) ? p.A1 : p.A0;
-            const int2* u_cur = (level & 1) ? p.U1 : p.U0;
-            uint64_t* f_cur = (level & 1) ? p.F1 : p.F0;
             MsLevel L;
             L.level = level;
             L.f_next = (level & 1) ? p.F0 : p.F1;
@@ -525,25 +591,49 @@ __device__ void msbfs_body(const ParamsMS& p) {
             L.u_next = (level & 1) ? p.U0 : p.U1;
             L.next = nxt;
             L.ef = 0;
+            L.cnt = 0;
+            L.lanes = 0;
+            L.live = live;
+            L.qbuf = sm.qbuf + warp * MS_QBUF;
+            L.qn = 0;
             if (dir == BFS_DIR_PULL) ms_pull_level(p, g, L, sm, f_cur);
-            else ms_push_level<T>(p, g, L, sm, a_cur, u_cur, f_cur, a, nunits, nxt);
+            else ms_push_level<T>(p, g, L, sm, a_cur, u_cur, f_cur, a, nunits);
+            const uint64_t ln = warp_or64(L.lanes);
+            if ((threadIdx.x & 31) == 0 && ln) atomicOr((unsigned long long*)&nxt->lanes, (unsigned long long)ln);
             unsigned long long ef = warp_sum(L.ef);
-            if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = ef;
+            unsigned long long cn = warp_sum(L.cnt);
+            if ((threadIdx.x & 31) == 0) sm.red[warp] = ef;
             __syncthreads();
             if (threadIdx.x == 0) {
                 unsigned long long t = 0;
                 for (int i = 0; i < T / 32; ++i) t += sm.red[i];
                 if (t) atomicAdd(&nxt->e_f, t);
             }
+            __syncthreads();
+            if (dir == BFS_DIR_PULL) {
+                if ((threadIdx.x & 31) == 0) sm.red[warp] = cn;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned long long t = 0;
+                    for (int i = 0; i < T / 32; ++i) t += sm.red[i];
+                    if (t) atomicAdd(&nxt->a_len, t);
+                }
+            } else {
+                list_valid = level + 1;
+            }
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
-            // F_i is consumed: clear its masks (they become the next target);
-            // after a push level, fold F_{i+1} into seen.
-            for (long long q = gtid; q < a; q += gthreads) f_cur[__ldcg(a_cur + q)] = 0;
+            // F_i is consumed: clear its masks (the buffer is F_{i+2}'s); after
+            // a push level fold F_{i+1} into seen (a pull level already did)
+            if (list_valid >= level) {
+                for (long long q = gtid; q < a; q += gthreads) f_cur[a_cur[q]] = 0;
+            } else {
+                for (long long v = gtid; v < g.n; v += gthreads) f_cur[v] = 0;
+            }
             if (dir != BFS_DIR_PULL) {
                 long long an = (long long)__ldcg(&nxt->a_len);
                 for (long long q = gtid; q < an; q += gthreads) {
-                    int v = __ldcg(L.a_next + q);
-                    p.seen[v] |= __ldcg((const unsigned long long*)L.f_next + v);
+                    int v = L.a_next[q];
+                    p.seen[v] |= ((const unsigned long long*)L.f_next)[v];
                 }
             }
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -556,7 +646,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(T) msbfs_kernel(ParamsMS p) {
+__global__ void __launch_bounds__(T, 2) msbfs_kernel(ParamsMS p) {
     msbfs_body<T>(p);
     if (threadIdx.x == 0) {
         int e = ld_volatile_i32(&p.ctl->bar.err);
@@ -564,7 +654,6 @@ __global__ void __launch_bounds__(T) msbfs_kernel(ParamsMS p) {
     }
 }
 
-constexpr int MS_T = 512;
 
 __global__ void ms_count_units_kernel(const int32_t* row_ptr, int32_t n, int32_t chunk, unsigned long long* out) {
     unsigned long long s = 0;
