@@ -130,12 +130,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ["common.cuh", "level.cuh", "policy_dev.cuh", "bfs_single.cu"]
+
+
 def source_hash() -> str:
-    """Hash of the CUDA sources: a recorded ncu traffic figure is only valid for this code."""
+    """Hash of the single-source kernel's sources: recorded ncu traffic is valid only for this code."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_17106_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

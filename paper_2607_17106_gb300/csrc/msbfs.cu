@@ -55,6 +55,7 @@ struct CtlMS {
     GridBarrier bar;
     CountersMS slot[3];
     int32_t levels;
+    unsigned long long long_len;  // deferred long rows of the current pull level
 };
 
 struct WorkspaceMS {
@@ -70,6 +71,8 @@ struct WorkspaceMS {
     MsUnit* d_units = nullptr;
     int32_t units_cap = 0;
     CtlMS* h_ctl = nullptr;
+    int32_t* longv = nullptr;            // pull: deferred long rows of the level
+    unsigned long long* acc_long = nullptr;  // their lanes found so far
 };
 
 void free_wsms(WorkspaceMS* w) {
@@ -83,6 +86,8 @@ void free_wsms(WorkspaceMS* w) {
     cudaFree(w->ctl);
     cudaFree(w->d_sticky);
     cudaFree(w->d_units);
+    cudaFree(w->longv);
+    cudaFree(w->acc_long);
     cudaFreeHost(w->h_ctl);
     delete w;
 }
@@ -121,6 +126,8 @@ struct ParamsMS {
     int32_t max_levels;
     bfs_level_record* log;  // per-level records of the first unit
     int32_t log_cap;
+    int32_t* longv;
+    unsigned long long* acc_long;
 };
 
 // Unit fields kept in registers / shared memory while a unit runs.
@@ -138,7 +145,9 @@ struct UnitView {
 };
 
 constexpr int MS_T = 512;
-constexpr int MS_QBUF = 64;  // per-warp staging of active-list appends
+constexpr int MS_QBUF = 64;       // per-warp staging of active-list appends
+constexpr int MS_LONG_ROW = 1024; // pull rows longer than this are scanned grid-wide
+constexpr int MS_LONG_ITEMS = 4;  // entries a thread tests per long-row chunk
 
 struct MsSmem {
     int32_t* depth[64];
@@ -353,6 +362,23 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             beg = __ldg(g.csc_ptr + v);
             end = __ldg(g.csc_ptr + v + 1);
         }
+        // rows longer than MS_LONG_ROW are scanned by the whole grid after
+        // this pass (ms_long_rows); defer them
+        const bool longrow = miss != 0 && end - beg > MS_LONG_ROW;
+        const unsigned lm = __ballot_sync(0xffffffffu, longrow);
+        if (lm) {
+            unsigned long long base = 0;
+            const int leader = __ffs(lm) - 1;
+            if ((int)lane == leader) base = atomicAdd(&p.ctl->long_len, (unsigned long long)__popc(lm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (longrow) {
+                const unsigned long long r = base + __popc(lm & lanemask_lt());
+                p.longv[r] = (int)v;
+                p.acc_long[r] = 0;
+                miss = 0;
+                end = beg;
+            }
+        }
         uint64_t acc = 0;
         int j = beg;
         const int lim = min(end, beg + p.pull_serial);
@@ -412,6 +438,88 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             L.cnt += 1;
             L.ef += (unsigned long long)(g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
         }
+    }
+}
+
+// Long rows of a pull level: each is scanned by a whole CTA (rows dealt
+// round-robin), MS_LONG_ITEMS*T entries per step, stopping once every live
+// missing lane is found.  The CTA ORs the supplied lanes in shared memory and
+// keeps the first supplier of each lane as its parent; it owns the row, so
+// the accumulator and the parents are written with plain stores.
+template <int T>
+__device__ void ms_long_rows(const ParamsMS& p, const UnitView& g, MsSmem& sm, const uint64_t* f_cur, uint64_t live,
+                             long long nl) {
+    __shared__ unsigned long long s_or;
+    __shared__ int s_prov[64];
+    const unsigned long long* F = (const unsigned long long*)f_cur;
+    const int per = MS_LONG_ITEMS * T;
+    for (long long r = blockIdx.x; r < nl; r += gridDim.x) {
+        const int v = p.longv[r];
+        const int beg = __ldg(g.csc_ptr + v), end = __ldg(g.csc_ptr + v + 1);
+        const uint64_t miss = live & ~((const unsigned long long*)p.seen)[v];
+        if (threadIdx.x == 0) s_or = 0;
+        __syncthreads();
+        for (int lo = beg; lo < end; lo += per) {
+            if ((s_or & miss) == miss) break;  // CTA-uniform: read after the barrier below
+            const int hi = min(end, lo + per);
+#pragma unroll
+            for (int k = 0; k < MS_LONG_ITEMS; ++k) {
+                const int e = lo + k * T + (int)threadIdx.x;
+                if (e < hi) {
+                    const int u = __ldg(g.csc_col + e);
+                    const uint64_t got = F[u] & miss;
+                    if (got) {
+                        const uint64_t old = atomicOr(&s_or, (unsigned long long)got);
+                        uint64_t nb = got & ~old;
+                        while (nb) {
+                            const int b = __ffsll((long long)nb) - 1;
+                            s_prov[b] = u;
+                            nb &= nb - 1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const uint64_t acc = s_or;
+        if (threadIdx.x == 0) p.acc_long[r] = acc;
+        if (threadIdx.x < 64 && ((acc >> threadIdx.x) & 1ull) && sm.parent[threadIdx.x])
+            sm.parent[threadIdx.x][v] = s_prov[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// The deferred long rows found their lanes: depth, F_{i+1}, seen and the
+// level counters (after ms_long_rows, before the next level).
+__device__ void ms_long_finalize(const ParamsMS& p, const UnitView& g, MsSmem& sm, uint64_t* f_next, long long nl,
+                                 int dnext, CountersMS* nxt) {
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    unsigned long long cnt = 0, ef = 0;
+    uint64_t ln = 0;
+    for (long long r = gtid; r < nl; r += gthreads) {
+        const uint64_t acc = __ldcg(p.acc_long + r);
+        if (!acc) continue;
+        const int v = p.longv[r];
+        ((unsigned long long*)f_next)[v] = acc;
+        ((unsigned long long*)p.seen)[v] |= acc;
+        uint64_t b = acc;
+        while (b) {
+            const int j = __ffsll((long long)b) - 1;
+            sm.depth[j][v] = dnext;
+            b &= b - 1;
+        }
+        cnt += 1;
+        ef += (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
+        ln |= acc;
+    }
+    cnt = warp_sum(cnt);
+    ef = warp_sum(ef);
+    ln = warp_or64(ln);
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) atomicAdd(&nxt->a_len, cnt);
+        if (ef) atomicAdd(&nxt->e_f, ef);
+        if (ln) atomicOr((unsigned long long*)&nxt->lanes, (unsigned long long)ln);
     }
 }
 
@@ -622,6 +730,16 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 list_valid = level + 1;
             }
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            long long nl = 0;
+            if (dir == BFS_DIR_PULL) {
+                nl = (long long)__ldcg(&ctl->long_len);
+                if (nl > 0) {
+                    ms_long_rows<T>(p, g, sm, f_cur, live, nl);
+                    if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+                    ms_long_finalize(p, g, sm, L.f_next, nl, level + 1, nxt);
+                }
+            }
+            if (gtid == 0) ctl->long_len = 0;
             // F_i is consumed: clear its masks (the buffer is F_{i+2}'s); after
             // a push level fold F_{i+1} into seen (a pull level already did)
             if (list_valid >= level) {
@@ -692,6 +810,8 @@ static bfs_status alloc_wsms(int32_t ncap, int64_t ucap, int32_t chunk, int32_t 
     ok = ok && cudaMalloc(&w->ctl, sizeof(CtlMS)) == cudaSuccess;
     ok = ok && cudaMalloc(&w->d_sticky, 4) == cudaSuccess && cudaMemset(w->d_sticky, 0, 4) == cudaSuccess;
     ok = ok && cudaMalloc(&w->d_units, sizeof(MsUnit) * (size_t)units_cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->longv, (size_t)ncap * 4) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->acc_long, (size_t)ncap * 8) == cudaSuccess;
     ok = ok && cudaMallocHost(&w->h_ctl, sizeof(CtlMS)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -756,6 +876,8 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.max_levels = o.max_levels > 0 ? o.max_levels : INT32_MAX / 2;
     p.log = d_log;
     p.log_cap = d_log ? o.level_log_cap : 0;
+    p.longv = w->longv;
+    p.acc_long = w->acc_long;
     int blocks = coop_blocks_ms(o.blocks_per_sm);
     void* args[] = {(void*)&p};
     BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, 0, st));
