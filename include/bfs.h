@@ -215,9 +215,16 @@ bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max
 #define BFS_MLP_NPARAM 1507
 #define BFS_MLP_NNORM 20
 
-/* Features of one level (host or device float[10]) from its counters. */
+/*
+ * Features of one level (host or device float[10]) from its counters: f =
+ * |F_i|, e_f = degree sum over F_i, m_u = degree sum over unvisited vertices,
+ * f_prev = |F_{i-1}|, prev_dir = form of level i-1.  Mostly scale-free:
+ * log2 of e_f/m_u, f/n, m_u/m, mean frontier degree over mean degree,
+ * (f+1)/(f_prev+1); prev_dir one-hot (pull, push-bitmap); log2(1+level);
+ * log2(deg_max / mean degree); log2(n)/32.
+ */
 bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,
-                               int32_t prev_dir, float* out10);
+                               int64_t f_prev, int32_t prev_dir, float* out10);
 
 /*
  * Training signal of the policy: run the plain method (opt->policy, heuristic

@@ -96,7 +96,7 @@ def load(path: str = LIB_PATH):
         "bfs_level_stats": (st, [vp, vp, i32, vp, ctypes.POINTER(i32), vp]),
         "bfs_profile_levels": (st, [vp, i32, ctypes.POINTER(bfs_options), i32, i32, vp, vp, vp,
                                     ctypes.POINTER(i32), vp]),
-        "bfs_policy_features": (st, [vp, i32, i64, i64, i64, i32, vp]),
+        "bfs_policy_features": (st, [vp, i32, i64, i64, i64, i64, i32, vp]),
         "bfs_policy_load": (st, [vp, i32, ctypes.POINTER(vp)]),
         "bfs_policy_weights": (st, [vp, vp, i32]),
         "bfs_policy_free": (None, [vp]),
@@ -236,10 +236,10 @@ class Graph:
         L = lv.value
         return X[:L].copy(), T[:L].copy(), taken[:L].copy()
 
-    def features(self, level, f, e_f, m_u, prev_dir) -> np.ndarray:
+    def features(self, level, f, e_f, m_u, f_prev, prev_dir) -> np.ndarray:
         x = np.empty(BFS_MLP_IN, np.float32)
-        _check(load().bfs_policy_features(self.handle, int(level), int(f), int(e_f), int(m_u), int(prev_dir),
-                                          _ptr(x)))
+        _check(load().bfs_policy_features(self.handle, int(level), int(f), int(e_f), int(m_u), int(f_prev),
+                                          int(prev_dir), _ptr(x)))
         return x
 
     def free(self):

@@ -337,7 +337,6 @@ bfs_status sync_graph(bfs_graph* g, cudaStream_t st) {
     return BFS_OK;
 }
 
-static float flog2(double x) { return (float)std::log2(x); }
 
 // Kernel parameters of one single-source run (workspace, graph, options).
 static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o, const float* mlp_dev, int32_t src_value,
@@ -371,9 +370,7 @@ static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o,
     p.beta = o.beta;
     p.gamma = o.gamma;
     p.mlp = mlp_dev;
-    p.log_n = flog2((double)g->n);
-    p.log_m = flog2(1.0 + (double)g->m);
-    p.log_degmax = flog2(1.0 + (double)g->deg_max);
+    p.deg_max = g->deg_max;
     p.chunk = o.chunk;
     p.medium = o.medium;
     p.pull_serial = o.pull_serial;
@@ -550,8 +547,8 @@ extern "C" bfs_status bfs_profile_levels(const bfs_graph* gc, int32_t source, co
         const Counters& c = h.slot[L % 3];
         if (h.done || c.q_len == 0) break;
         long long m_u = L > 0 ? h.m_u - (long long)c.e_f : h.m_u;
-        policy_features(features + (size_t)L * BFS_MLP_IN, (long long)c.q_len, (long long)c.e_f, m_u, L, h.prev_dir,
-                        g->n, p.log_n, p.log_m, p.log_degmax);
+        policy_features(features + (size_t)L * BFS_MLP_IN, (long long)c.q_len, (long long)c.e_f, m_u, h.f_prev, L,
+                        h.prev_dir, g->n, g->m, g->deg_max);
         uint32_t* f_cur = (L & 1) ? w->F[1] : w->F[0];
         e = cudaMemcpyAsync(snapP, w->P, w->W * 4, cudaMemcpyDeviceToDevice, st);
         if (!e) e = cudaMemcpyAsync(snapF, f_cur, w->W * 4, cudaMemcpyDeviceToDevice, st);

@@ -92,7 +92,7 @@ struct Params1 {
     const int8_t* schedule;
     int32_t schedule_len;
     const float* mlp;
-    float log_n, log_m, log_degmax;
+    int32_t deg_max;
     // tuning
     int32_t chunk, medium, pull_serial, aggregate;
     int64_t timeout_ns;
@@ -127,7 +127,7 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
                 // warp 0 evaluates; result broadcast through shared memory
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
-                        policy_features(s_feat, f, e_f, m_u, level, prev_dir, p.n, p.log_n, p.log_m, p.log_degmax);
+                        policy_features(s_feat, f, e_f, m_u, f_prev, level, prev_dir, p.n, p.m, p.deg_max);
                     __syncwarp();
                     int a = policy_argmax_warp(p.mlp, s_feat);
                     if (threadIdx.x == 0) *s_mlp_out = (float)a;
@@ -224,6 +224,13 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
         bit = 1u << (v & 31);
         want = !(p.P[w] & bit);  // may be stale (bits only grow): the OR decides
     }
+    // the row bounds of a likely claim are fetched before the OR so that both
+    // round trips overlap
+    int rb = 0, re = 0;
+    if (want) {
+        rb = __ldg(p.row_ptr + v);
+        re = __ldg(p.row_ptr + v + 1);
+    }
     bool claimed = false;
     if (p.aggregate) {
         unsigned act = __ballot_sync(0xffffffffu, want);
@@ -242,9 +249,7 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
     } else if (want) {
         claimed = !(atomicOr(p.P + w, bit) & bit);
     }
-    int deg = 0;
-    if (claimed) deg = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
-    emit(p, L, claimed, v, u, deg);
+    emit(p, L, claimed, v, u, claimed ? re - rb : 0);
 }
 
 // ------------------------------------------------------------ push tiles
@@ -370,7 +375,7 @@ __device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
 }
 
 // Pull level (Section 5, loop order d -> s): one warp per 32-vertex word of P
-// (lane = vertex), words dealt round-robin over all warps of the grid.  An
+// (lane = vertex); warps take blocks of 32 words round-robin.  An
 // unvisited lane scans its in-neighbours in ascending order and stops at the
 // first one in F_i (ANY = the lowest-index frontier neighbour); rows longer
 // than `pull_serial` entries are finished by the whole warp 32 entries at a
@@ -386,68 +391,103 @@ __device__ __forceinline__ void pull_level_words(const Params1& p, LevelCtx& L, 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int dnext = L.level + 1;
     const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
-    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.W; w += nwarps) {
-        const unsigned pw = ld_word<NC>(p.P, w);
-        if (pw == 0xffffffffu) {
-            if (lane == 0) f_next[w] = 0;
-            continue;
-        }
-        const long long v = w * 32 + lane;
-        const bool unvis = !((pw >> lane) & 1u);
-        int beg = 0, end = 0;
-        if (unvis) {
-            beg = __ldg(p.csc_ptr + v);
-            end = __ldg(p.csc_ptr + v + 1);
-        }
-        bool found = false;
-        int par = -1;
-        int j = beg;
-        const int lim = min(end, beg + serial);
-        for (; j < lim; ++j) {
-            const int u = __ldg(p.csc_col + j);
-            if ((ld_word<NC>(f_cur, u >> 5) >> (u & 31)) & 1u) {
-                found = true;
-                par = u;
-                break;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // each warp reads 32 words of P at once; fully visited words get an empty
+    // F_{i+1} word, the others are finished two at a time
+    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
+        const long long wl = wb + lane;
+        const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
+        if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
+        unsigned todo = __ballot_sync(0xffffffffu, pwl != 0xffffffffu);
+        while (todo) {
+            int wi[2];
+            unsigned pw[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                wi[k] = todo ? __ffs(todo) - 1 : -1;
+                if (todo) todo &= todo - 1;
+                pw[k] = __shfl_sync(0xffffffffu, pwl, wi[k] < 0 ? 0 : wi[k]);
+                if (wi[k] < 0) pw[k] = 0xffffffffu;
             }
-        }
-        unsigned rm = __ballot_sync(0xffffffffu, unvis && !found && j < end);
-        while (rm) {
-            const int l = __ffs(rm) - 1;
-            const int bl = __shfl_sync(0xffffffffu, j, l);
-            const int el = __shfl_sync(0xffffffffu, end, l);
-            int hit = -1;
-            for (int base = bl; base < el; base += 32) {
-                const int idx = base + (int)lane;
-                int uu = 0;
-                bool h = false;
-                if (idx < el) {
-                    uu = __ldg(p.csc_col + idx);
-                    h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+            bool unvis[2], found[2];
+            int beg[2], end[2], j[2], par[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                unvis[k] = !((pw[k] >> lane) & 1u);
+                const long long v = (wb + wi[k]) * 32 + lane;
+                beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
+                end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
+                j[k] = beg[k];
+                found[k] = false;
+                par[k] = -1;
+            }
+            // ascending scans of both rows advance together
+            for (int step = 0; step < serial; ++step) {
+                int u[2];
+                bool live = false;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const bool lk = !found[k] && j[k] < end[k];
+                    u[k] = lk ? __ldg(p.csc_col + j[k]) : -1;
+                    live |= lk;
                 }
-                const unsigned hb = __ballot_sync(0xffffffffu, h);
-                if (hb) {
-                    hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                    break;
+                if (!live) break;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (u[k] >= 0) {
+                        if ((ld_word<NC>(f_cur, u[k] >> 5) >> (u[k] & 31)) & 1u) {
+                            found[k] = true;
+                            par[k] = u[k];
+                        } else {
+                            ++j[k];
+                        }
+                    }
                 }
             }
-            if ((int)lane == l && hit >= 0) {
-                found = true;
-                par = hit;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (wi[k] < 0) break;  // warp-uniform
+                unsigned rm = __ballot_sync(0xffffffffu, unvis[k] && !found[k] && j[k] < end[k]);
+                while (rm) {
+                    const int l = __ffs(rm) - 1;
+                    const int bl = __shfl_sync(0xffffffffu, j[k], l);
+                    const int el = __shfl_sync(0xffffffffu, end[k], l);
+                    int hit = -1;
+                    for (int base = bl; base < el; base += 32) {
+                        const int idx = base + (int)lane;
+                        int uu = 0;
+                        bool h = false;
+                        if (idx < el) {
+                            uu = __ldg(p.csc_col + idx);
+                            h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+                        }
+                        const unsigned hb = __ballot_sync(0xffffffffu, h);
+                        if (hb) {
+                            hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
+                            break;
+                        }
+                    }
+                    if ((int)lane == l && hit >= 0) {
+                        found[k] = true;
+                        par[k] = hit;
+                    }
+                    rm &= rm - 1;
+                }
+                const long long w = wb + wi[k];
+                const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
+                if (lane == 0) {
+                    f_next[w] = nb;
+                    if (nb) p.P[w] = pw[k] | nb;
+                }
+                if (found[k]) {
+                    const long long v = w * 32 + lane;
+                    L.depth[v] = dnext;
+                    if (L.parent) L.parent[v] = par[k];
+                    L.ef += (unsigned long long)(p.symmetric ? (end[k] - beg[k])
+                                                             : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+                    L.cnt += 1;
+                }
             }
-            rm &= rm - 1;
-        }
-        const unsigned nb = __ballot_sync(0xffffffffu, found);
-        if (lane == 0) {
-            f_next[w] = nb;
-            if (nb) p.P[w] = pw | nb;
-        }
-        if (found) {
-            L.depth[v] = dnext;
-            if (L.parent) L.parent[v] = par;
-            L.ef += (unsigned long long)(p.symmetric ? (end - beg)
-                                                     : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
-            L.cnt += 1;
         }
     }
 }

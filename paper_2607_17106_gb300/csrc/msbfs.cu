@@ -556,8 +556,7 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
             if (p.mlp) {
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
-                        policy_features(sm.feat, a, e_f, m_u, level, prev_dir, g.n, log2f((float)g.n),
-                                        log2f(1.0f + (float)g.m), log2f(1.0f + (float)deg_max));
+                        policy_features(sm.feat, a, e_f, m_u, a_prev, level, prev_dir, g.n, g.m, deg_max);
                     __syncwarp();
                     int c = policy_argmax_warp(p.mlp, sm.feat);
                     if (threadIdx.x == 0) sm.mlp_out = (float)c;

@@ -245,11 +245,10 @@ extern "C" bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const
 }
 
 extern "C" bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,
-                                          int32_t prev_dir, float* out10) {
+                                          int64_t f_prev, int32_t prev_dir, float* out10) {
     if (!g || !out10) return fail(BFS_EINVAL, "null argument");
     float x[MLP_IN];
-    policy_features(x, f, e_f, m_u, level, prev_dir, g->n, (float)std::log2((double)g->n),
-                    (float)std::log2(1.0 + (double)g->m), (float)std::log2(1.0 + (double)g->deg_max));
+    policy_features(x, f, e_f, m_u, f_prev, level, prev_dir, g->n, g->m, g->deg_max);
     if (is_device_ptr(out10)) {
         BFS_CUDA(cudaMemcpy(out10, x, sizeof(x), cudaMemcpyHostToDevice));
     } else {

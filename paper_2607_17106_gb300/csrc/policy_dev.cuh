@@ -24,21 +24,30 @@ constexpr int OFF_ISTD = NPARAM + MLP_IN;
 constexpr int NWEIGHTS = NPARAM + 2 * MLP_IN;
 static_assert(NPARAM == BFS_MLP_NPARAM, "parameter count");
 
-// Ten per-level features: log2 sizes of the frontier, its edges and the
-// unexplored edges, graph size, level, densities, degree spread, previous form.
-__host__ __device__ inline void policy_features(float* x, long long f, long long e_f, long long m_u, int level,
-                                                int prev_dir, int n, float log_n, float log_m, float log_degmax) {
-    x[0] = log2f(1.0f + (float)f);
-    x[1] = log2f(1.0f + (float)e_f);
-    x[2] = log2f(1.0f + (float)(m_u > 0 ? m_u : 0));
-    x[3] = log_n;
-    x[4] = log_m;
-    x[5] = log2f(1.0f + (float)level);
-    x[6] = (float)f / (float)n;
-    float r = (float)e_f / (float)(m_u > 1 ? m_u : 1);
-    x[7] = r < 64.0f ? r : 64.0f;
-    x[8] = log_degmax;
-    x[9] = (prev_dir == BFS_DIR_PULL) ? 1.0f : 0.0f;
+// Ten per-level features, scale-free where possible so that a policy
+// trained on small graphs transfers to larger ones:
+//   x0 log2(e_f / m_u)         frontier edges over unexplored edges (Beamer's ratio)
+//   x1 log2(f / n)             frontier density
+//   x2 log2(m_u / m)           fraction of the edges still unexplored
+//   x3 log2(deg(F) / deg(G))   mean frontier degree over mean degree
+//   x4 log2((f+1) / (f'+1))    frontier growth since the previous level
+//   x5 previous level was pull        x6 previous level was push-bitmap
+//   x7 log2(1 + level)         x8 log2(deg_max / deg(G))   x9 log2(n) / 32
+__host__ __device__ inline void policy_features(float* x, long long f, long long e_f, long long m_u, long long f_prev,
+                                                int level, int prev_dir, long long n, long long m, int deg_max) {
+    const float fn = (float)(f > 1 ? f : 1), ef = (float)(e_f > 1 ? e_f : 1), mu = (float)(m_u > 1 ? m_u : 1);
+    const float nn = (float)(n > 1 ? n : 1), mm = (float)(m > 1 ? m : 1);
+    const float dmean = mm / nn;
+    x[0] = log2f(ef / mu);
+    x[1] = log2f(fn / nn);
+    x[2] = log2f(mu / mm);
+    x[3] = log2f((ef / fn) / dmean);
+    x[4] = log2f((float)(f + 1) / (float)(f_prev + 1));
+    x[5] = (prev_dir == BFS_DIR_PULL) ? 1.0f : 0.0f;
+    x[6] = (prev_dir == BFS_DIR_PUSH_BITMAP) ? 1.0f : 0.0f;
+    x[7] = log2f(1.0f + (float)level);
+    x[8] = log2f((float)(deg_max > 1 ? deg_max : 1) / dmean);
+    x[9] = log2f(nn) / 32.0f;
 }
 
 #ifdef __CUDACC__

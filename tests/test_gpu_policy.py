@@ -117,8 +117,16 @@ def test_profile_levels_records_every_level_of_the_plain_method():
         f, e_f = st[i][0], st[i][1]
         if i > 0:
             m_u -= e_f
-        ref = g.features(i, f, e_f, m_u, taken[i - 1] if i > 0 else bg.BFS_DIR_PUSH_QUEUE)
+        f_prev = st[i - 1][0] if i > 0 else 0
+        ref = g.features(i, f, e_f, m_u, f_prev, taken[i - 1] if i > 0 else bg.BFS_DIR_PUSH_QUEUE)
         assert np.allclose(X[i], ref), (i, X[i], ref)
+        # the features follow their stated definitions
+        n, m = adj.n, adj.m
+        dmean = m / n
+        assert abs(X[i][0] - np.log2(max(e_f, 1) / max(m_u, 1))) < 1e-4
+        assert abs(X[i][1] - np.log2(max(f, 1) / n)) < 1e-4
+        assert abs(X[i][4] - np.log2((f + 1) / (f_prev + 1))) < 1e-4
+        assert abs(X[i][3] - np.log2((max(e_f, 1) / max(f, 1)) / dmean)) < 1e-4
     # the profiled search left a correct search behind: a normal run still matches
     depth = torch.empty(n, dtype=torch.int32, device="cuda")
     g.run(np.array([src], np.int32), depth, None, bg.options(batch=0))
