@@ -56,6 +56,21 @@ def dist_env():
     return ws, rank, local
 
 
+def describe(w) -> str:
+    p = w.params
+    if w.kind == "rmat":
+        d = 1 - p["a"] - p["b"] - p["c"]
+        return (f"RMAT scale {p['scale']}, edge factor {p['edge_factor']}, a={p['a']} b={p['b']} c={p['c']} "
+                f"d={d:.2f}")
+    if w.kind == "er":
+        return f"Erdos-Renyi n={p['n']}, {p['m_pairs']} pairs (mean degree {2 * p['m_pairs'] / p['n']:.0f})"
+    if w.kind == "grid":
+        return f"{p['width']}x{p['height']} 4-neighbour grid, {int(100 * p['p_del'])}% edges deleted, relabelled"
+    if w.kind == "ba":
+        return f"Barabasi-Albert n={p['n']}, m={p['m']}"
+    return w.kind
+
+
 # ------------------------------------------------------------ roofline model
 def bytes_model(stats: np.ndarray, n: int):
     """Minimum DRAM bytes of one search from its per-level statistics.
@@ -228,6 +243,83 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ mixed batch
+MIXED = "mixed-rmat16-22-q256"
+
+
+def run_mixed_bench(args, bg, torch):
+    """256 queries over RMAT graphs of scales 16..22 (edge factor 16, seeds 16..22),
+    the graph of each query drawn uniformly (seed 106): one bfs_run_mixed launch
+    against the same queries as per-graph 64-lane batches and one at a time."""
+    scales = list(range(16, 23))
+    graphs, edges_of = [], []
+    for sc in scales:
+        n, s, d = graphgen.rmat(sc, 16, seed=sc)
+        graphs.append((n, bg.Graph.build(n, s, d)))
+        edges_of.append((s, d))
+    q = 256
+    goq = np.random.default_rng(106).integers(0, len(scales), q).astype(np.int32)
+    srcs = np.zeros(q, np.int32)
+    for gi in range(len(scales)):
+        idx = np.flatnonzero(goq == gi)
+        if len(idx):
+            n, _ = graphs[gi]
+            srcs[idx] = graphgen.sample_sources(n, *edges_of[gi], len(idx), 106 + gi)
+    depth = [torch.empty(graphs[gi][0], dtype=torch.int32, device="cuda") for gi in goq]
+    parent = [torch.empty(graphs[gi][0], dtype=torch.int32, device="cuda") for gi in goq]
+    gl = [g for _, g in graphs]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def mixed_once():
+        bg.run_mixed(gl, goq, srcs, depth, parent, bg.options())
+
+    for _ in range(args.warmup):
+        mixed_once()
+    torch.cuda.synchronize()
+    ref = [dd.cpu().numpy() for dd in depth]
+    edges = 0.0
+    for i, gi in enumerate(goq):
+        st = gl[gi].level_stats(depth[i])
+        edges += teps_edges(st)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mixed_once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mixed = e0.elapsed_time(e1) / args.steps
+    ok = all(np.array_equal(depth[i].cpu().numpy(), ref[i]) for i in range(q))
+    # the same queries per graph as ordinary 64-lane batches, and one at a time
+    e0.record(stream)
+    for gi in range(len(scales)):
+        idx = np.flatnonzero(goq == gi)
+        n = graphs[gi][0]
+        for c0 in range(0, len(idx), 64):
+            part = idx[c0:c0 + 64]
+            dd = torch.empty((len(part), n), dtype=torch.int32, device="cuda")
+            gl[gi].run(srcs[part], dd, None, bg.options())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_graph = e0.elapsed_time(e1)
+    e0.record(stream)
+    for i, gi in enumerate(goq):
+        gl[gi].run(np.array([srcs[i]], np.int32), depth[i], parent[i], bg.options(batch=0))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1)
+    line = {"metric": "BFS GTEPS, mixed batch of 256 queries over RMAT scales 16-22 in one persistent launch",
+            "value": edges / (ms_mixed * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": MIXED + ": 256 queries, graph of each uniform over RMAT scales 16..22 (edge "
+                                          "factor 16, a=0.57 b=c=0.19, seeds 16..22)", "edges_per_step": edges},
+            "gpu_launches": args.steps, "depth_repeatable": ok,
+            "per_graph_batches": {"ms": ms_per_graph, "gteps": edges / (ms_per_graph * 1e-3) / 1e9},
+            "one_at_a_time": {"ms": ms_single, "gteps": edges / (ms_single * 1e-3) / 1e9}}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -246,6 +338,8 @@ def main():
     bgbuild.build()
     bg.load()
     stream = torch.cuda.current_stream()
+    if args.workload == MIXED:
+        return run_mixed_bench(args, bg, torch)
 
     w = graphgen.WORKLOADS[args.workload]
     n, src, dst = w.edges()
@@ -314,51 +408,62 @@ def main():
 
     extra = {}
     if not args.no_extra:
-        # batched: the same sources as one 64-lane MS-BFS launch
-        optb = bg.options(batch=1)
-        for _ in range(3):
-            g.run(sources, depth, parent, optb)
-        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
-        e0.record(stream)
-        for _ in range(reps):
-            g.run(sources, depth, parent, optb)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        g.sync()
-        bms = e0.elapsed_time(e1) / reps
-        same = bool(np.array_equal(depth.cpu().numpy(), depth_h))
-        extra["batched_msbfs"] = {"gteps": edges / (bms * 1e-3) / 1e9, "ms_per_step": bms,
-                                  "speedup_vs_plain": ms_per_step / bms, "depth_equal_to_plain": same}
-        if os.path.exists(args.policy_weights):
-            pol = bg.Policy(np.load(args.policy_weights))
-            optl = bg.options(batch=0, policy=bg.BFS_POLICY_MLP, mlp=pol)
-            for _ in range(2):
-                for j in range(k):
-                    g.run(np.array([sources[j]], np.int32), depth[j], parent[j], optl)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for j in range(k):
-                g.run(np.array([sources[j]], np.int32), depth[j], parent[j], optl)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            g.sync()
-            lms = e0.elapsed_time(e1)
-            extra["learned_single"] = {"gteps": edges / (lms * 1e-3) / 1e9, "ms_per_step": lms,
-                                       "speedup_vs_plain": ms_per_step / lms,
-                                       "depth_equal_to_plain": bool(np.array_equal(depth.cpu().numpy(), depth_h))}
-            optbl = bg.options(batch=1, policy=bg.BFS_POLICY_MLP, mlp=pol)
-            g.run(sources, depth, parent, optbl)
+
+        def time_batched(o, reps=3):
+            """ms per launch of the k sources as 64-lane MS-BFS batches (device time)."""
+            g.run(sources, depth, parent, o)
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(reps):
-                g.run(sources, depth, parent, optbl)
+                g.run(sources, depth, parent, o)
             e1.record(stream)
             torch.cuda.synchronize()
-            blms = e0.elapsed_time(e1) / reps
+            g.sync()
+            return e0.elapsed_time(e1) / reps
+
+        def time_single(o, count=None):
+            """ms for the first `count` sources one at a time (device time)."""
+            js = range(k if count is None else min(count, k))
+            for j in js:
+                g.run(np.array([sources[j]], np.int32), depth[j], parent[j], o)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for j in js:
+                g.run(np.array([sources[j]], np.int32), depth[j], parent[j], o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g.sync()
+            return e0.elapsed_time(e1), len(js)
+
+        def same_depths():
+            return bool(np.array_equal(depth.cpu().numpy(), depth_h))
+
+        bms = time_batched(bg.options(batch=1))
+        extra["batched_msbfs"] = {"gteps": edges / (bms * 1e-3) / 1e9, "ms_per_step": bms,
+                                  "speedup_vs_plain": ms_per_step / bms, "depth_equal_to_plain": same_depths()}
+        try:
+            from paper_2607_17106_gb300 import tune
+            ot = tune.tuned_options(w.kind, n, info.m, batch=True)
+            tms = time_batched(ot)
+            extra["batched_tuned"] = {"gteps": edges / (tms * 1e-3) / 1e9, "ms_per_step": tms,
+                                      "speedup_vs_plain": ms_per_step / tms, "depth_equal_to_plain": same_depths(),
+                                      "options": {f: getattr(ot, f) for f in ("chunk", "medium", "pull_serial",
+                                                                              "alpha", "beta")}}
+        except Exception as exc:  # no cache entry for this device/graph class
+            extra["batched_tuned"] = {"skipped": str(exc)[:120]}
+        gms, cnt = time_single(bg.options(batch=0, mode=bg.BFS_MODE_GRAPH), 8)
+        pms, _ = time_single(bg.options(batch=0), 8)
+        extra["graph_mode_single"] = {"sources": cnt, "ms_graph_mode": gms, "ms_persistent": pms,
+                                      "graph_over_persistent": gms / pms}
+        if os.path.exists(args.policy_weights):
+            pol = bg.Policy(np.load(args.policy_weights))
+            lms, _ = time_single(bg.options(batch=0, policy=bg.BFS_POLICY_MLP, mlp=pol))
+            extra["learned_single"] = {"gteps": edges / (lms * 1e-3) / 1e9, "ms_per_step": lms,
+                                       "speedup_vs_plain": ms_per_step / lms, "depth_equal_to_plain": same_depths()}
+            blms = time_batched(bg.options(batch=1, policy=bg.BFS_POLICY_MLP, mlp=pol))
             extra["batched_learned"] = {"gteps": edges / (blms * 1e-3) / 1e9, "ms_per_step": blms,
-                                        "speedup_vs_plain": ms_per_step / blms}
+                                        "speedup_vs_plain": ms_per_step / blms, "depth_equal_to_plain": same_depths()}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()
@@ -385,9 +490,8 @@ def main():
             "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{w.name}: RMAT scale 22, edge factor 16, a=0.57 b=c=0.19 d=0.05, "
-                                   f"symmetrised+dedup, n={n}, m={info.m} directed; {k} seeded sources "
-                                   f"one at a time", "sources_per_step": k, "edges_per_step": edges,
+            "config": {"workload": f"{w.name}: {describe(w)}, symmetrised+dedup, n={n}, m={info.m} directed; "
+                                   f"{k} seeded sources one at a time", "sources_per_step": k, "edges_per_step": edges,
                        "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
                        "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=14 beta=24"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": k * args.steps,
