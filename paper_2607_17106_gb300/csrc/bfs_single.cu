@@ -229,10 +229,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     }
 }
 
-// 64 registers a thread so that 1024 threads fit on an SM with the pull
-// level's shared memory (32 warps of memory-level parallelism).
+// At most 40 registers a thread for T <= 512, so that 1536 threads (48 warps
+// of memory-level parallelism for the latency-bound gathers) fit on an SM.
 template <int T>
-__global__ void __launch_bounds__(T, (1024 / T) > 0 ? (1024 / T) : 1) bfs1_kernel(Params1 p) {
+__global__ void __launch_bounds__(T, (1536 / T) > 0 ? (1536 / T) : 1) bfs1_kernel(Params1 p) {
     bfs1_body<T>(p);
     if (threadIdx.x == 0) {
         int e = ld_volatile_i32(&p.ctl->bar.err);

@@ -198,6 +198,31 @@ __device__ __forceinline__ void emit_units(const Params1& p, int2* u_out, Counte
     }
 }
 
+// Chunk units of the big rows among a warp's claims: one atomic per warp.
+// Warp-uniform call.
+__device__ __forceinline__ void emit_units_warp(const Params1& p, int2* u_out, Counters* c, bool big, int v, int deg) {
+    const unsigned bm = __ballot_sync(0xffffffffu, big);
+    if (!bm) return;
+    const unsigned lane = lane_id();
+    int nch = big ? (deg + p.chunk - 1) / p.chunk : 0;
+    int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&c->u_len, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + total > (unsigned long long)p.ucap) {
+        if (lane == 0) atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
+        return;
+    }
+    const unsigned long long off = base + (incl - nch);
+    for (int k = 0; k < nch; ++k) u_out[off + k] = make_int2(v, k);
+}
+
 // Record vertices claimed in a push level: depth/parent, staged next-queue
 // slot, degree sum, chunk units for big rows.  Warp-uniform call.
 __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int deg) {
@@ -210,9 +235,9 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
         L.depth[v] = L.level + 1;
         if (L.parent) L.parent[v] = u;
         L.ef += (unsigned long long)deg;
-        if (deg >= p.chunk) emit_units(p, L.u_next, L.next, v, deg);
     }
     L.qn += c;
+    emit_units_warp(p, L.u_next, L.next, claimed && deg >= p.chunk, v, deg);
 }
 
 // Push candidate (u -> v): claim v in P if not yet visited.  Warp-uniform.
@@ -339,8 +364,12 @@ __device__ __forceinline__ void push_unit(const Params1& p, LevelCtx& L, int2 un
 template <int T>
 __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int32_t* q_cur,
                            const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, bool units_valid) {
+    // queue tiles hold about f / gridDim vertices (at most T), so that a small
+    // frontier is spread over every CTA instead of a few full tiles
+    long long per_tile = (f + gridDim.x - 1) / gridDim.x;
+    per_tile = per_tile < 1 ? 1 : (per_tile > T ? T : per_tile);
     long long ntiles;
-    if (dir == BFS_DIR_PUSH_QUEUE) ntiles = (f + T - 1) / T;
+    if (dir == BFS_DIR_PUSH_QUEUE) ntiles = (f + per_tile - 1) / per_tile;
     else ntiles = (p.W + (T / 32) - 1) / (T / 32);
     if (!units_valid) nunits = 0;
     long long nitems = nunits + ntiles;
@@ -351,8 +380,8 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
             long long t = it - nunits;
             int u = -1;
             if (dir == BFS_DIR_PUSH_QUEUE) {
-                long long q = t * T + threadIdx.x;
-                if (q < f) u = __ldcg(q_cur + q);
+                long long q = t * per_tile + threadIdx.x;
+                if (threadIdx.x < per_tile && q < f) u = __ldcg(q_cur + q);
             } else {
                 long long w = t * (T / 32) + (threadIdx.x >> 5);
                 if (w < p.W) {

@@ -306,7 +306,9 @@ __device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, M
 template <int T>
 __device__ void ms_push_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const int32_t* a_cur,
                               const int2* u_cur, const uint64_t* f_cur, long long a, long long nunits) {
-    long long nitems = nunits + (a + T - 1) / T;
+    long long per_tile = (a + gridDim.x - 1) / gridDim.x;
+    per_tile = per_tile < 1 ? 1 : (per_tile > T ? T : per_tile);
+    long long nitems = nunits + (a + per_tile - 1) / per_tile;
     for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
         if (it < nunits) {
             int2 un = u_cur[it];
@@ -321,8 +323,8 @@ __device__ void ms_push_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
                 ms_candidate(p, g, L, sm, has, v, u, fu);
             }
         } else {
-            long long q = (it - nunits) * T + threadIdx.x;
-            int u = q < a ? a_cur[q] : -1;
+            long long q = (it - nunits) * per_tile + threadIdx.x;
+            int u = (threadIdx.x < per_tile && q < a) ? a_cur[q] : -1;
             ms_push_tile<T>(p, g, L, sm, u, f_cur);
         }
     }
