@@ -201,6 +201,26 @@ bfs_status bfs_run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const
 bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
                            int32_t* levels, void* cuda_stream);
 
+/*
+ * bfs_level_stats without any allocation.  The paper has no counterpart; this
+ * exists for callers that must not allocate memory while they run: a serving
+ * process whose device memory is reserved up front by its own allocator, code
+ * that may not take the driver's allocation lock, or a program that audits
+ * that no allocation happens after start-up.  All scratch lives in one
+ * file-scope device array of fixed size (about 360 KB, held by every GPU that
+ * loads the library until the process exits), so at most 4096 levels are
+ * supported: a larger max_levels, or a search with more levels, returns
+ * BFS_ERANGE.  depth[n] must be device memory; stats (6*max_levels int64, the
+ * same table as bfs_level_stats) may be host or device; *levels (host)
+ * receives L.  The first call on a device looks up the scratch array's device
+ * address, so make that first call before any stream capture.  Every call
+ * shares the one array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Synchronises
+ * `cuda_stream`.  Errors: EINVAL, ERANGE, ECUDA.
+ */
+bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
+                                   int32_t* levels, void* cuda_stream);
+
 /* ----------------------------------------------------- learned policy (MLP) */
 /*
  * Direction policy: an FP32 MLP 10 -> 32 -> 32 -> 3 (ReLU) whose argmax picks

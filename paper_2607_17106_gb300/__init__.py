@@ -35,7 +35,8 @@ BFS_MLP_NPARAM, BFS_MLP_NNORM = 1507, 20
 
 EXPORTED = [
     "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_free_graph", "bfs_options_init", "bfs_run",
-    "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_profile_levels", "bfs_policy_features", "bfs_policy_load",
+    "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_level_stats_noalloc", "bfs_profile_levels",
+    "bfs_policy_features", "bfs_policy_load",
     "bfs_policy_weights", "bfs_policy_free", "bfs_policy_forward", "bfs_policy_train_step",
     "bfs_policy_set_norm", "bfs_status_string", "bfs_last_error", "bfs_version",
 ]
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
         "bfs_run_mixed": (st, [ctypes.POINTER(vp), i32, vp, vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                ctypes.POINTER(bfs_options), vp]),
         "bfs_level_stats": (st, [vp, vp, i32, vp, ctypes.POINTER(i32), vp]),
+        "bfs_level_stats_noalloc": (st, [vp, vp, i32, vp, ctypes.POINTER(i32), vp]),
         "bfs_profile_levels": (st, [vp, i32, ctypes.POINTER(bfs_options), i32, i32, vp, vp, vp,
                                     ctypes.POINTER(i32), vp]),
         "bfs_policy_features": (st, [vp, i32, i64, i64, i64, i64, i32, vp]),

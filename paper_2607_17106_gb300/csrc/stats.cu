@@ -150,3 +150,108 @@ extern "C" bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, 
     }
     return rc;
 }
+
+// ------------------------------------------------------------ no-allocation variant
+// bfs_level_stats for callers that may not allocate device memory: all of its
+// scratch lives in one file-scope __device__ array of fixed size, so the call
+// makes no cudaMalloc/cudaFree (nor any other allocating runtime call).
+namespace bfsgb {
+namespace {
+
+constexpr int NOALLOC_MAX_LEVELS = 4096;
+
+struct NoallocScratch {
+    int max_depth;
+    int pad[63];
+    unsigned long long consts[2];
+    unsigned long long arrays[5 * NOALLOC_MAX_LEVELS];
+    long long table[6 * NOALLOC_MAX_LEVELS];
+};
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+__global__ void noalloc_clear_kernel(NoallocScratch* s) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 5 * NOALLOC_MAX_LEVELS; i += gridDim.x * blockDim.x)
+        s->arrays[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->max_depth = -1;
+        s->consts[0] = 0;
+        s->consts[1] = 0;
+    }
+}
+
+// The six statistics per level from the accumulated difference arrays.
+__global__ void noalloc_table_kernel(NoallocScratch* s, int L) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const unsigned long long* a = s->arrays;
+    long long u = 0, eu = 0;
+    for (int i = 0; i < L; ++i) {
+        u += (long long)a[2 * L + i];
+        eu += (long long)a[3 * L + i];
+        long long* o = s->table + 6 * (long long)i;
+        o[0] = (long long)a[0 * L + i];
+        o[1] = (long long)a[1 * L + i];
+        o[2] = u + (long long)s->consts[0];
+        o[5] = eu + (long long)s->consts[1];
+        o[3] = o[5] - (long long)a[4 * L + i];
+        o[4] = (i + 1 < L) ? (long long)a[0 * L + i + 1] : 0;
+    }
+}
+
+std::mutex g_noalloc_lock;
+NoallocScratch* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device with that device current).
+bfs_status noalloc_scratch(NoallocScratch** out) {
+    int dev = device_id();
+    if (dev < 0 || dev >= 64) return fail(BFS_EINVAL, "device index %d not supported", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_lock);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = (NoallocScratch*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return BFS_OK;
+}
+
+}  // namespace
+}  // namespace bfsgb
+
+extern "C" bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int32_t max_levels,
+                                              int64_t* stats, int32_t* levels, void* cuda_stream) {
+    if (!g || !depth || !stats || !levels) return fail(BFS_EINVAL, "null argument");
+    if (max_levels <= 0) return fail(BFS_EINVAL, "max_levels must be positive");
+    if (max_levels > NOALLOC_MAX_LEVELS)
+        return fail(BFS_ERANGE, "max_levels %d exceeds the fixed scratch limit of %d levels", max_levels,
+                    NOALLOC_MAX_LEVELS);
+    if (!is_device_ptr(depth)) return fail(BFS_EINVAL, "depth must be device memory");
+    NoallocScratch* s = nullptr;
+    bfs_status rc = noalloc_scratch(&s);
+    if (rc != BFS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int blocks = num_sms() * 4;
+    noalloc_clear_kernel<<<num_sms(), 256, 0, st>>>(s);
+    max_depth_kernel<<<blocks, 256, 0, st>>>(depth, g->n, &s->max_depth);
+    int h_max = -1;
+    BFS_CUDA(cudaMemcpyAsync(&h_max, &s->max_depth, 4, cudaMemcpyDeviceToHost, st));
+    BFS_CUDA(cudaStreamSynchronize(st));
+    const int L = h_max + 1;
+    if (L > max_levels) return fail(BFS_ERANGE, "search has %d levels, max_levels = %d", L, max_levels);
+    *levels = L;
+    if (L <= 0) return BFS_OK;
+    const size_t sm = (size_t)5 * L * 8;
+    if (sm <= 48 * 1024) {
+        level_accum_kernel<true><<<blocks, 256, sm, st>>>(g->row_ptr, g->col, depth, g->n, L, s->arrays, s->consts);
+    } else {
+        level_accum_kernel<false><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, depth, g->n, L, s->arrays, s->consts);
+    }
+    noalloc_table_kernel<<<1, 1, 0, st>>>(s, L);
+    BFS_CUDA(cudaGetLastError());
+    BFS_CUDA(cudaMemcpyAsync(stats, s->table, (size_t)6 * L * sizeof(int64_t), cudaMemcpyDefault, st));
+    BFS_CUDA(cudaStreamSynchronize(st));
+    return BFS_OK;
+}
