@@ -133,9 +133,9 @@ typedef struct {
     int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (256) */
     int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
     int32_t pull_serial;     /* pull: entries of one row tested per flattened warp round (32; MS-BFS: twice this many entries are scanned per thread before a warp takes over) */
-    int32_t block_threads;   /* threads per CTA of the level kernels (512) */
+    int32_t block_threads;   /* threads per CTA of the persistent single-source kernel: 256, 512 or 1024 (1024) */
     int32_t blocks_per_sm;   /* CTAs per SM, 0 = as many as fit (persistent/cooperative launch) */
-    int32_t claim_aggregate; /* push: warp-aggregate the visited-bitmap OR by word (1) */
+    int32_t claim_aggregate; /* push: warp-aggregate the visited-bitmap OR by word (0) */
     int64_t barrier_timeout_ns; /* limit of one device-side wait before BFS_ETIMEOUT (2e9) */
     const int8_t* schedule;  /* host array for BFS_POLICY_SCHEDULE */
     int32_t schedule_len;

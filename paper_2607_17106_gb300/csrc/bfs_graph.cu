@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.cnt = 0;
     L.qbuf = sm.qbuf + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
+    L.precheck = push_precheck(ctl->m_u, p.m);
     const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const int2* u_cur = (level & 1) ? p.U1 : p.U0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
@@ -207,11 +208,12 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     }
 }
 
-// Pull level at full occupancy (few registers): pull_level_words with
+// Pull level at full occupancy (few registers): pull_level with
 // non-coherent loads of P and F_i, which no CTA writes during this kernel
 // except the word owner after its last read.
 __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     __shared__ unsigned long long s_ef[PULL_T / 32], s_cn[PULL_T / 32];
+    __shared__ PullWarpSmem s_pull[PULL_T / 32];
     Ctl1* ctl = p.ctl;
     const int level = ctl->cur_level;
     LevelCtx L;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     L.cnt = 0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     uint32_t* f_next = (level & 1) ? p.F0 : p.F1;
-    pull_level_words<true>(p, L, f_cur, f_next);
+    pull_level<true>(p, L, f_cur, f_next, s_pull[threadIdx.x >> 5]);
     unsigned long long ef = warp_sum(L.ef);
     unsigned long long cn = warp_sum(L.cnt);
     if (lane_id() == 0) {

@@ -68,6 +68,7 @@ void free_ws1(Workspace1* w) {
 template <int T>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
+    __shared__ PullWarpSmem s_pull[T / 32];
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
     Ctl1* ctl = p.ctl;
@@ -184,8 +185,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.cnt = 0;
         L.qbuf = sm.qbuf + warp * QBUF;
         L.qn = 0;
+        L.precheck = push_precheck(m_u, p.m);
         if (dir == BFS_DIR_PULL) {
-            pull_level_words<false>(p, L, f_cur, f_nxt);
+            pull_level<false>(p, L, f_cur, f_nxt, s_pull[warp]);
         } else {
             push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
         }

@@ -88,9 +88,9 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->chunk = 256;
     o->medium = 32;
     o->pull_serial = 32;
-    o->block_threads = 512;
+    o->block_threads = 1024;
     o->blocks_per_sm = 0;
-    o->claim_aggregate = 1;
+    o->claim_aggregate = 0;
     o->barrier_timeout_ns = 2000000000ll;
     o->batch = 1;
 }

@@ -83,6 +83,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -108,21 +111,24 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsi
     target += nblocks;
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        atomicAdd(&b->count, 1u);
+        // the release add publishes every write of this CTA made before the
+        // __syncthreads above; the acquire load that sees the last arrival
+        // makes all CTAs' writes visible to this CTA after the one below
+        red_release_add_u32(&b->count, 1u);
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
         while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
-            if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
-            if ((++spins & 63u) == 1 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) {
-                atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);
-                atomicExch(&b->abort, 1);
-                ok = 0;
-                break;
+            if ((++spins & 31u) == 0) {
+                if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
+                if ((int64_t)(globaltimer_ns() - t0) > timeout_ns) {
+                    atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);
+                    atomicExch(&b->abort, 1);
+                    ok = 0;
+                    break;
+                }
             }
         }
         if (ld_volatile_i32(&b->abort)) ok = 0;
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

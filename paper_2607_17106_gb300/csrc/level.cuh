@@ -172,7 +172,12 @@ struct LevelCtx {
     unsigned long long cnt; // this thread's share of |F_{i+1}| (pull levels)
     int32_t* qbuf;          // this warp's staging buffer (QBUF entries)
     int qn;                 // entries staged (warp-uniform)
+    bool precheck;          // push: read P before the OR (most targets already visited)
 };
+
+// A push target is visited with probability about 1 - m_u / m (the explored
+// share of the edges); reading P before the OR pays once most are.
+__device__ __forceinline__ bool push_precheck(long long m_u, long long m) { return 2 * m_u < m; }
 
 // Move the warp's staged queue entries to the next queue: one atomic per
 // flush instead of one per claiming round.  Warp-uniform.
@@ -247,7 +252,7 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
     if (has) {
         w = (unsigned)v >> 5;
         bit = 1u << (v & 31);
-        want = !(p.P[w] & bit);  // may be stale (bits only grow): the OR decides
+        want = !L.precheck || !(p.P[w] & bit);  // may be stale (bits only grow): the OR decides
     }
     // the row bounds of a likely claim are fetched before the OR so that both
     // round trips overlap
@@ -282,6 +287,7 @@ template <int T>
 struct TileSmem {
     int off[T + 1];
     int beg[T];
+    int lim[T];
     int src[T];
     int scan_tmp[33];
     int32_t qbuf[(T / 32) * QBUF];
@@ -300,21 +306,31 @@ __device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSme
         end = __ldg(p.row_ptr + u + 1);
         if (skip_big && end - beg >= p.chunk) end = beg;
     }
-    // medium rows: one warp each
-    bool med = (end - beg) >= p.medium;
-    unsigned mm = __ballot_sync(0xffffffffu, med);
-    while (mm) {
-        int l = __ffs(mm) - 1;
-        int ub = __shfl_sync(0xffffffffu, u, l);
-        int bb = __shfl_sync(0xffffffffu, beg, l);
-        int ee = __shfl_sync(0xffffffffu, end, l);
-        for (int base = bb; base < ee; base += 32) {
-            int j = base + (int)lane;
-            bool has = j < ee;
-            int v = has ? __ldg(p.col + j) : 0;
-            push_candidate(p, L, has, v, ub);
+    // medium rows: cut into 32-edge segments that the CTA's warps take in
+    // turn (a warp walking only its own lanes' rows would serialise them while
+    // the other warps idle)
+    const bool med = (end - beg) >= p.medium;
+    int nseg_total;
+    const int soff = block_exclusive_scan(med ? (end - beg + 31) >> 5 : 0, sm.scan_tmp, &nseg_total);
+    if (nseg_total > 0) {
+        sm.off[threadIdx.x] = soff;
+        sm.beg[threadIdx.x] = beg;
+        sm.lim[threadIdx.x] = end;
+        sm.src[threadIdx.x] = u;
+        __syncthreads();
+        for (int s = (int)(threadIdx.x >> 5); s < nseg_total; s += T / 32) {
+            // the row holding segment s: largest t with off[t] <= s
+            int lo = 0, hi = T - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (sm.off[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            const int j = sm.beg[lo] + ((s - sm.off[lo]) << 5) + (int)lane;
+            const bool has = j < sm.lim[lo];
+            const int v = has ? __ldg(p.col + j) : 0;
+            push_candidate(p, L, has, v, sm.src[lo]);
         }
-        mm &= mm - 1;
+        // the scan below passes a barrier before anything overwrites off/beg/src
     }
     if (med) end = beg;
     // small rows: flatten (u, j) pairs over the CTA
@@ -360,12 +376,12 @@ __device__ __forceinline__ void push_unit(const Params1& p, LevelCtx& L, int2 un
 
 // Push level: items are [chunk units of F_i] then [tiles of the frontier],
 // dealt to CTAs round-robin (units are equal-sized; tiles hold rows below
-// the chunk size).
+// the chunk size).  Queue tiles hold about f / gridDim vertices (at most T),
+// so that a small frontier is spread over every CTA instead of a few full
+// tiles.
 template <int T>
 __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int32_t* q_cur,
                            const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, bool units_valid) {
-    // queue tiles hold about f / gridDim vertices (at most T), so that a small
-    // frontier is spread over every CTA instead of a few full tiles
     long long per_tile = (f + gridDim.x - 1) / gridDim.x;
     per_tile = per_tile < 1 ? 1 : (per_tile > T ? T : per_tile);
     long long ntiles;
@@ -397,127 +413,367 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
 
 // ------------------------------------------------------------ pull level
 constexpr int PULL_SERIAL_MAX = 32;  // row entries one lane scans before its warp takes over
+#ifndef BFS_PULL_R
+#define BFS_PULL_R 1
+#endif
+// in-neighbours a lane loads and tests per serial step: the loads of one step
+// are independent, so a step costs about one memory round trip whatever R is
+constexpr int PULL_R = BFS_PULL_R;
 
 template <bool NC>
 __device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
     return NC ? __ldg(a + i) : a[i];
 }
 
-// Pull level (Section 5, loop order d -> s): one warp per 32-vertex word of P
-// (lane = vertex); warps take blocks of 32 words round-robin.  An
-// unvisited lane scans its in-neighbours in ascending order and stops at the
-// first one in F_i (ANY = the lowest-index frontier neighbour); rows longer
-// than `pull_serial` entries are finished by the whole warp 32 entries at a
-// time.  The warp writes the word of P and of F_{i+1} with plain stores (it
-// owns the word) and counts |F_{i+1}| and e_f in registers.  NC selects
-// non-coherent loads of P and F_i, valid when no other CTA writes them during
-// the kernel (the graph-mode kernel); the persistent kernel uses ordinary
-// loads ordered by its grid barrier.
+// Dense block of a pull level: the warp finishes the block's words two at a
+// time, lane = vertex.  An unvisited lane scans its in-neighbours in ascending
+// order and stops at the first one in F_i (ANY = the lowest-index frontier
+// neighbour); rows longer than `pull_serial` entries are finished by the
+// whole warp 32 entries at a time.  The warp writes the words of P and of
+// F_{i+1} with plain stores (it owns them).  Warp-uniform.
 template <bool NC>
-__device__ __forceinline__ void pull_level_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
-                                                 uint32_t* f_next) {
+__device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
+                                                 uint32_t* f_next, long long wb, unsigned pwl) {
     const unsigned lane = lane_id();
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int dnext = L.level + 1;
     const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // each warp reads 32 words of P at once; fully visited words get an empty
-    // F_{i+1} word, the others are finished two at a time
-    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
-        const long long wl = wb + lane;
-        const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
-        if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
-        unsigned todo = __ballot_sync(0xffffffffu, pwl != 0xffffffffu);
-        while (todo) {
-            int wi[2];
-            unsigned pw[2];
+    const long long wl = wb + lane;
+    if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, pwl != 0xffffffffu);
+    while (todo) {
+        int wi[2];
+        unsigned pw[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            wi[k] = todo ? __ffs(todo) - 1 : -1;
+            if (todo) todo &= todo - 1;
+            pw[k] = __shfl_sync(0xffffffffu, pwl, wi[k] < 0 ? 0 : wi[k]);
+            if (wi[k] < 0) pw[k] = 0xffffffffu;
+        }
+        bool unvis[2], found[2];
+        int beg[2], end[2], j[2], par[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            unvis[k] = !((pw[k] >> lane) & 1u);
+            const long long v = (wb + wi[k]) * 32 + lane;
+            beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
+            end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
+            j[k] = beg[k];
+            found[k] = false;
+            par[k] = -1;
+        }
+        // ascending scans of both rows advance together, PULL_R entries a step;
+        // the first frontier entry in row order is the parent
+        for (int step = 0; step < serial; step += PULL_R) {
+            int u[2][PULL_R];
+            unsigned fw[2][PULL_R];
+            bool live = false;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                wi[k] = todo ? __ffs(todo) - 1 : -1;
-                if (todo) todo &= todo - 1;
-                pw[k] = __shfl_sync(0xffffffffu, pwl, wi[k] < 0 ? 0 : wi[k]);
-                if (wi[k] < 0) pw[k] = 0xffffffffu;
+                const bool lk = !found[k] && j[k] < end[k];
+#pragma unroll
+                for (int r = 0; r < PULL_R; ++r)
+                    u[k][r] = (lk && j[k] + r < end[k]) ? __ldg(p.csc_col + j[k] + r) : -1;
+                live |= lk;
             }
-            bool unvis[2], found[2];
-            int beg[2], end[2], j[2], par[2];
+            if (!live) break;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int r = 0; r < PULL_R; ++r) fw[k][r] = u[k][r] >= 0 ? ld_word<NC>(f_cur, u[k][r] >> 5) : 0u;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                unvis[k] = !((pw[k] >> lane) & 1u);
-                const long long v = (wb + wi[k]) * 32 + lane;
-                beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
-                end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
-                j[k] = beg[k];
-                found[k] = false;
-                par[k] = -1;
-            }
-            // ascending scans of both rows advance together
-            for (int step = 0; step < serial; ++step) {
-                int u[2];
-                bool live = false;
+                if (u[k][0] < 0) continue;
+                int adv = PULL_R;
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const bool lk = !found[k] && j[k] < end[k];
-                    u[k] = lk ? __ldg(p.csc_col + j[k]) : -1;
-                    live |= lk;
-                }
-                if (!live) break;
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (u[k] >= 0) {
-                        if ((ld_word<NC>(f_cur, u[k] >> 5) >> (u[k] & 31)) & 1u) {
-                            found[k] = true;
-                            par[k] = u[k];
-                        } else {
-                            ++j[k];
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (wi[k] < 0) break;  // warp-uniform
-                unsigned rm = __ballot_sync(0xffffffffu, unvis[k] && !found[k] && j[k] < end[k]);
-                while (rm) {
-                    const int l = __ffs(rm) - 1;
-                    const int bl = __shfl_sync(0xffffffffu, j[k], l);
-                    const int el = __shfl_sync(0xffffffffu, end[k], l);
-                    int hit = -1;
-                    for (int base = bl; base < el; base += 32) {
-                        const int idx = base + (int)lane;
-                        int uu = 0;
-                        bool h = false;
-                        if (idx < el) {
-                            uu = __ldg(p.csc_col + idx);
-                            h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
-                        }
-                        const unsigned hb = __ballot_sync(0xffffffffu, h);
-                        if (hb) {
-                            hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                            break;
-                        }
-                    }
-                    if ((int)lane == l && hit >= 0) {
-                        found[k] = true;
-                        par[k] = hit;
-                    }
-                    rm &= rm - 1;
-                }
-                const long long w = wb + wi[k];
-                const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
-                if (lane == 0) {
-                    f_next[w] = nb;
-                    if (nb) p.P[w] = pw[k] | nb;
-                }
-                if (found[k]) {
-                    const long long v = w * 32 + lane;
-                    L.depth[v] = dnext;
-                    if (L.parent) L.parent[v] = par[k];
-                    L.ef += (unsigned long long)(p.symmetric ? (end[k] - beg[k])
-                                                             : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
-                    L.cnt += 1;
+                for (int r = PULL_R - 1; r >= 0; --r)
+                    if (u[k][r] >= 0 && ((fw[k][r] >> (u[k][r] & 31)) & 1u)) adv = r;
+                if (adv < PULL_R) {
+                    found[k] = true;
+                    par[k] = u[k][adv];
+                    j[k] += adv;
+                } else {
+                    j[k] += PULL_R;
                 }
             }
         }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (wi[k] < 0) break;  // warp-uniform
+            unsigned rm = __ballot_sync(0xffffffffu, unvis[k] && !found[k] && j[k] < end[k]);
+            while (rm) {
+                const int l = __ffs(rm) - 1;
+                const int bl = __shfl_sync(0xffffffffu, j[k], l);
+                const int el = __shfl_sync(0xffffffffu, end[k], l);
+                int hit = -1;
+                for (int base = bl; base < el; base += 32) {
+                    const int idx = base + (int)lane;
+                    int uu = 0;
+                    bool h = false;
+                    if (idx < el) {
+                        uu = __ldg(p.csc_col + idx);
+                        h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+                    }
+                    const unsigned hb = __ballot_sync(0xffffffffu, h);
+                    if (hb) {
+                        hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
+                        break;
+                    }
+                }
+                if ((int)lane == l && hit >= 0) {
+                    found[k] = true;
+                    par[k] = hit;
+                }
+                rm &= rm - 1;
+            }
+            const long long w = wb + wi[k];
+            const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
+            if (lane == 0) {
+                f_next[w] = nb;
+                if (nb) p.P[w] = pw[k] | nb;
+            }
+            if (found[k]) {
+                const long long v = w * 32 + lane;
+                L.depth[v] = dnext;
+                if (L.parent) L.parent[v] = par[k];
+                L.ef += (unsigned long long)(p.symmetric ? (end[k] - beg[k])
+                                                         : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+                L.cnt += 1;
+            }
+        }
+    }
+}
+
+// Sparse block of a pull level (same ANY reading as pull_block_pairs): the
+// lanes take the unvisited vertices of the block in ascending order and each
+// lane runs its scans as a pipeline of one memory step per iteration:
+//   bounds  csc_ptr[v], csc_ptr[v+1]
+//   first   csc_col[j]
+//   test    the F_i word of the current in-neighbour, and csc_col[j+1]
+// so a lane whose scan ends (hit, row exhausted) takes the next vertex at
+// once instead of idling until the slowest lane of its word finishes.  After
+// `pull_serial` tested entries a row is deferred to the block's long-row list,
+// scanned by the whole warp 32 entries at a time.  New bits of the block's
+// words collect in shared memory; the warp then writes its words of F_{i+1}
+// and P with plain stores (it owns them).
+struct PullWarpSmem {
+    unsigned nb[32];                   // new bits of the block's words
+    int lv[32], lj[32], le[32], lb[32];  // deferred rows: vertex, next entry, end, row start
+    int nl;
+};
+
+// Position of the r-th (0-based) set bit of m; m must have more than r bits set.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const unsigned lo = m & ((1u << s) - 1u);
+        const int c = __popc(lo);
+        if (r >= c) {
+            r -= c;
+            m >>= s;
+            pos += s;
+        } else {
+            m = lo;
+        }
+    }
+    return pos;
+}
+
+// Record a vertex found by a pull scan (parent u).  Any lane, any time.
+__device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWarpSmem& ws, long long wb, int v, int u,
+                                           int b0, int e) {
+    atomicOr(&ws.nb[(int)(((long long)v >> 5) - wb)], 1u << (v & 31));
+    L.depth[v] = L.level + 1;
+    if (L.parent) L.parent[v] = u;
+    L.ef += (unsigned long long)(p.symmetric ? (e - b0) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+    L.cnt += 1;
+}
+
+// The deferred rows of the block, each scanned by the whole warp.  Warp-uniform.
+template <bool NC>
+__device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, PullWarpSmem& ws, long long wb,
+                                               const uint32_t* f_cur) {
+    __syncwarp();
+    const int nl = min(ws.nl, 32);
+    const unsigned lane = lane_id();
+    for (int r = 0; r < nl; ++r) {
+        const int v = ws.lv[r], jl = ws.lj[r], el = ws.le[r], bl = ws.lb[r];
+        for (int base = jl; base < el; base += 32) {
+            const int idx = base + (int)lane;
+            int uu = 0;
+            bool h = false;
+            if (idx < el) {
+                uu = __ldg(p.csc_col + idx);
+                h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+            }
+            const unsigned hb = __ballot_sync(0xffffffffu, h);
+            if (hb) {
+                const int hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
+                if (lane == 0) pull_found(p, L, ws, wb, v, hit, bl, el);
+                break;
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) ws.nl = 0;
+    __syncwarp();
+}
+
+constexpr int PULL_SLOTS = 2;       // vertices a lane scans at once in a sparse block
+constexpr int PULL_SPARSE_MAX = 384;  // unvisited vertices (of 1024) up to which a block is sparse
+
+// Pull level (Section 5, loop order d -> s).  Warps take blocks of 32 words
+// of P (1024 vertices) round-robin.  A block with many unvisited vertices,
+// where most scans end at their first entries, is finished two words at a
+// time (pull_block_pairs: few instructions per vertex); a block with few
+// runs the lane pipeline below, which keeps every lane busy on the long
+// scans that dominate late levels.  |F_{i+1}| and e_f are counted in
+// registers.  NC selects non-coherent loads of P and F_i, valid when no other
+// CTA writes them during the kernel (the graph-mode kernel); the persistent
+// kernel uses ordinary loads ordered by its grid barrier.
+template <bool NC>
+__device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                           PullWarpSmem& ws) {
+    constexpr unsigned FULL = 0xffffffffu;
+    enum { IDLE = 0, BOUNDS = 1, FIRST = 2, TEST = 3 };
+    const unsigned lane = lane_id();
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int serial = max(1, min(p.pull_serial, PULL_SERIAL_MAX));
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
+        const long long wl = wb + lane;
+        const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
+        const unsigned um = ~pwl;  // unvisited vertices of this lane's word
+        const int c = __popc(um);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const int U = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - c;
+        if (U == 0) {  // warp-uniform: every vertex of the block is visited
+            if (wl < p.W) f_next[wl] = 0;
+            continue;
+        }
+        if (U > PULL_SPARSE_MAX) {
+            pull_block_pairs<NC>(p, L, f_cur, f_next, wb, pwl);
+            continue;
+        }
+        ws.nb[lane] = 0;
+        if (lane == 0) ws.nl = 0;
+        __syncwarp();
+        int next = 0;  // unvisited vertices of the block handed out (warp-uniform)
+        int st[PULL_SLOTS], v[PULL_SLOTS], j[PULL_SLOTS], e[PULL_SLOTS], b0[PULL_SLOTS], u[PULL_SLOTS],
+            tried[PULL_SLOTS];
+#pragma unroll
+        for (int q = 0; q < PULL_SLOTS; ++q) {
+            st[q] = IDLE;
+            v[q] = j[q] = e[q] = b0[q] = u[q] = tried[q] = 0;
+        }
+        // every iteration advances each busy slot by one step; a vertex takes
+        // at most serial + 2 steps of its slot before it ends or is deferred
+        const long long guard = (long long)U * (serial + 3) + 2;
+        for (long long it = 0;; ++it) {
+            // idle slots take the next unvisited vertices (ascending)
+#pragma unroll
+            for (int q = 0; q < PULL_SLOTS; ++q) {
+                const unsigned idle = __ballot_sync(FULL, st[q] == IDLE);
+                if (idle != 0 && next < U) {
+                    const int k = next + __popc(idle & lanemask_lt());
+                    int lo = 0;  // word of the k-th unvisited vertex: largest i with excl_i <= k
+#pragma unroll
+                    for (int s2 = 16; s2 > 0; s2 >>= 1) {
+                        const int ex = __shfl_sync(FULL, excl, (lo + s2) & 31);
+                        if (lo + s2 < 32 && ex <= k) lo += s2;
+                    }
+                    const unsigned umw = __shfl_sync(FULL, um, lo);
+                    const int exw = __shfl_sync(FULL, excl, lo);
+                    if (st[q] == IDLE && k < U) {
+                        v[q] = (int)((wb + lo) * 32 + nth_set_bit(umw, k - exw));
+                        st[q] = BOUNDS;
+                        tried[q] = 0;
+                    }
+                    next = min(U, next + __popc(idle));
+                }
+            }
+            bool busy = false;
+#pragma unroll
+            for (int q = 0; q < PULL_SLOTS; ++q) busy |= st[q] != IDLE;
+            if (!__any_sync(FULL, busy)) break;
+            if (it > guard) {  // cannot happen; stop rather than spin
+                if (lane == 0) atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
+                break;
+            }
+            // one memory step per busy slot, all issued before any is used
+            unsigned x1[PULL_SLOTS], x2[PULL_SLOTS];
+#pragma unroll
+            for (int q = 0; q < PULL_SLOTS; ++q) {
+                x1[q] = 0;
+                x2[q] = 0;
+                if (st[q] == BOUNDS) {
+                    x1[q] = (unsigned)__ldg(p.csc_ptr + v[q]);
+                    x2[q] = (unsigned)__ldg(p.csc_ptr + v[q] + 1);
+                } else if (st[q] == FIRST) {
+                    x1[q] = (unsigned)__ldg(p.csc_col + j[q]);
+                } else if (st[q] == TEST) {
+                    x1[q] = ld_word<NC>(f_cur, u[q] >> 5);
+                    if (j[q] + 1 < e[q]) x2[q] = (unsigned)__ldg(p.csc_col + j[q] + 1);
+                }
+            }
+            bool defer[PULL_SLOTS];
+#pragma unroll
+            for (int q = 0; q < PULL_SLOTS; ++q) {
+                defer[q] = false;
+                if (st[q] == BOUNDS) {
+                    b0[q] = (int)x1[q];
+                    j[q] = b0[q];
+                    e[q] = (int)x2[q];
+                    st[q] = (j[q] < e[q]) ? FIRST : IDLE;
+                } else if (st[q] == FIRST) {
+                    u[q] = (int)x1[q];
+                    st[q] = TEST;
+                } else if (st[q] == TEST) {
+                    if ((x1[q] >> (u[q] & 31)) & 1u) {
+                        pull_found(p, L, ws, wb, v[q], u[q], b0[q], e[q]);
+                        st[q] = IDLE;
+                    } else if (++j[q] >= e[q]) {
+                        st[q] = IDLE;
+                    } else {
+                        u[q] = (int)x2[q];
+                        defer[q] = ++tried[q] >= serial;
+                    }
+                }
+            }
+            // long rows go to the block's list; a full list is drained first
+#pragma unroll
+            for (int q = 0; q < PULL_SLOTS; ++q) {
+                const unsigned dm = __ballot_sync(FULL, defer[q]);
+                if (dm) {
+                    if (ws.nl + __popc(dm) > 32) pull_long_rows<NC>(p, L, ws, wb, f_cur);
+                    if (defer[q]) {
+                        const int slot = ws.nl + __popc(dm & lanemask_lt());
+                        ws.lv[slot] = v[q];
+                        ws.lj[slot] = j[q];
+                        ws.le[slot] = e[q];
+                        ws.lb[slot] = b0[q];
+                        st[q] = IDLE;
+                    }
+                    __syncwarp();
+                    if (lane == 0) ws.nl += __popc(dm);
+                    __syncwarp();
+                }
+            }
+        }
+        pull_long_rows<NC>(p, L, ws, wb, f_cur);
+        if (wl < p.W) {
+            const unsigned nb = ws.nb[lane];
+            f_next[wl] = nb;
+            if (nb) p.P[wl] = pwl | nb;
+        }
+        __syncwarp();
     }
 }
 

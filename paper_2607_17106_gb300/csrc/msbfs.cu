@@ -149,11 +149,17 @@ constexpr int MS_QBUF = 64;       // per-warp staging of active-list appends
 constexpr int MS_LONG_ROW = 1024; // pull rows longer than this are scanned grid-wide
 constexpr int MS_LONG_ITEMS = 4;  // entries a thread tests per long-row chunk
 
+#ifndef BFS_MS_PULL_R
+#define BFS_MS_PULL_R 4
+#endif
+constexpr int MS_PULL_R = BFS_MS_PULL_R;  // in-neighbours loaded per serial pull step
+
 struct MsSmem {
     int32_t* depth[64];
     int32_t* parent[64];
     int off[MS_T + 1];
     int beg[MS_T];
+    int lim[MS_T];
     int src[MS_T];
     unsigned long long fmask[MS_T];
     int scan_tmp[33];
@@ -247,6 +253,7 @@ __device__ __forceinline__ void ms_candidate(const ParamsMS& p, const UnitView& 
 template <int T>
 __device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, int u,
                              const uint64_t* f_cur) {
+    static_assert(T <= MS_T, "tile arrays are sized for MS_T threads");
     unsigned lane = lane_id();
     int beg = 0, end = 0;
     uint64_t fu = 0;
@@ -256,21 +263,28 @@ __device__ void ms_push_tile(const ParamsMS& p, const UnitView& g, MsLevel& L, M
         fu = ((const unsigned long long*)f_cur)[u];
         if (end - beg >= p.chunk) end = beg;  // chunk units cover it
     }
-    bool med = (end - beg) >= p.medium;
-    unsigned mm = __ballot_sync(0xffffffffu, med);
-    while (mm) {
-        int l = __ffs(mm) - 1;
-        int ub = __shfl_sync(0xffffffffu, u, l);
-        int bb = __shfl_sync(0xffffffffu, beg, l);
-        int ee = __shfl_sync(0xffffffffu, end, l);
-        uint64_t fl = __shfl_sync(0xffffffffu, (unsigned long long)fu, l);
-        for (int base = bb; base < ee; base += 32) {
-            int j = base + (int)lane;
-            bool has = j < ee;
-            int v = has ? __ldg(g.col + j) : 0;
-            ms_candidate(p, g, L, sm, has, v, ub, fl);
+    // medium rows: 32-edge segments taken in turn by every warp of the CTA
+    const bool med = (end - beg) >= p.medium;
+    int nseg_total;
+    const int soff = block_exclusive_scan(med ? (end - beg + 31) >> 5 : 0, sm.scan_tmp, &nseg_total);
+    if (nseg_total > 0) {
+        sm.off[threadIdx.x] = soff;
+        sm.beg[threadIdx.x] = beg;
+        sm.lim[threadIdx.x] = end;
+        sm.src[threadIdx.x] = u;
+        sm.fmask[threadIdx.x] = fu;
+        __syncthreads();
+        for (int s = (int)(threadIdx.x >> 5); s < nseg_total; s += T / 32) {
+            int lo = 0, hi = T - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (sm.off[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            const int j = sm.beg[lo] + ((s - sm.off[lo]) << 5) + (int)lane;
+            const bool has = j < sm.lim[lo];
+            const int v = has ? __ldg(g.col + j) : 0;
+            ms_candidate(p, g, L, sm, has, v, sm.src[lo], sm.fmask[lo]);
         }
-        mm &= mm - 1;
     }
     if (med) end = beg;
     int deg = end - beg, total;
@@ -384,17 +398,28 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
         uint64_t acc = 0;
         int j = beg;
         const int lim = min(end, beg + p.pull_serial);
-        for (; j < lim && acc != miss; ++j) {
-            const int u = __ldg(g.csc_col + j);
-            const uint64_t got = F[u] & miss & ~acc;
-            if (got) {
-                acc |= got;
-                uint64_t b = got;
-                while (b) {
-                    int lj = __ffsll((long long)b) - 1;
-                    if (sm.parent[lj]) sm.parent[lj][v] = u;
-                    b &= b - 1;
+        // MS_PULL_R entries per step (independent loads), tested in row order
+        while (j < lim && acc != miss) {
+            int uu[MS_PULL_R];
+            uint64_t fm[MS_PULL_R];
+#pragma unroll
+            for (int r = 0; r < MS_PULL_R; ++r) uu[r] = j + r < lim ? __ldg(g.csc_col + j + r) : -1;
+#pragma unroll
+            for (int r = 0; r < MS_PULL_R; ++r) fm[r] = uu[r] >= 0 ? F[uu[r]] : 0ull;
+#pragma unroll
+            for (int r = 0; r < MS_PULL_R; ++r) {
+                if (uu[r] < 0 || acc == miss) break;
+                const uint64_t got = fm[r] & miss & ~acc;
+                if (got) {
+                    acc |= got;
+                    uint64_t b = got;
+                    while (b) {
+                        int lj = __ffsll((long long)b) - 1;
+                        if (sm.parent[lj]) sm.parent[lj][v] = uu[r];
+                        b &= b - 1;
+                    }
                 }
+                ++j;
             }
         }
         unsigned rm = __ballot_sync(0xffffffffu, miss != 0 && acc != miss && j < end);

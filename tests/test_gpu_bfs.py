@@ -204,6 +204,17 @@ def test_other_graph_families(kind):
         _check(adj, srcs, dd, pp)
 
 
+@pytest.mark.parametrize("serial", [1, 3, 32])
+def test_pull_long_row_deferral(rmat14, serial):
+    # forced pull with a tiny serial budget: nearly every scan is deferred to
+    # the warp's long-row list, which fills and drains many times per block
+    n, adj, g, srcs = rmat14
+    for mode in (bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_GRAPH):
+        o = bg.options(batch=0, policy=bg.BFS_POLICY_PULL, pull_serial=serial, mode=mode)
+        dd, pp = _run(g, n, srcs[:4], o)
+        _check(adj, srcs[:4], dd, pp)
+
+
 def test_edge_cases_tiny_and_isolated():
     # one vertex, no edges
     g = bg.Graph.build(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
