@@ -147,6 +147,7 @@ struct UnitView {
 constexpr int MS_T = 512;
 constexpr int MS_QBUF = 64;       // per-warp staging of active-list appends
 constexpr int MS_LONG_ROW = 1024; // pull rows longer than this are scanned grid-wide
+static_assert(MS_LONG_ROW < 65536, "pull parent positions are staged as 16-bit row offsets");
 constexpr int MS_LONG_ITEMS = 4;  // entries a thread tests per long-row chunk
 
 #ifndef BFS_MS_PULL_R
@@ -359,8 +360,15 @@ __device__ __forceinline__ uint64_t warp_or64(uint64_t x) {
 // `pull_serial` entries are finished by the whole warp.  Depths are written
 // lane-major in a warp-uniform loop over the union of the new lanes, so the
 // 32 vertices' entries of one lane's depth row go out together.
+// Dynamic shared memory of the MS-BFS kernel: per warp, the row offset of
+// the parent found for each (lane l, vertex of the warp's word) in a pull
+// level, [l][vertex], so that parents are written lane-major like depths.
+constexpr size_t MS_PIDX_BYTES = (size_t)(MS_T / 32) * 64 * 32 * sizeof(unsigned short);
+extern __shared__ __align__(16) unsigned short ms_pidx_smem[];
+
 __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const uint64_t* f_cur) {
     const unsigned lane = lane_id();
+    unsigned short* pidx = ms_pidx_smem + (threadIdx.x >> 5) * (64 * 32);
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int dnext = L.level + 1;
     const long long W = (g.n + 31) >> 5;
@@ -415,7 +423,7 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
                     uint64_t b = got;
                     while (b) {
                         int lj = __ffsll((long long)b) - 1;
-                        if (sm.parent[lj]) sm.parent[lj][v] = uu[r];
+                        pidx[lj * 32 + lane] = (unsigned short)(j - beg);
                         b &= b - 1;
                     }
                 }
@@ -427,9 +435,9 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             const int l = __ffs(rm) - 1;
             const int jl = __shfl_sync(0xffffffffu, j, l);
             const int el = __shfl_sync(0xffffffffu, end, l);
+            const int bl = __shfl_sync(0xffffffffu, beg, l);
             const uint64_t ml = __shfl_sync(0xffffffffu, (unsigned long long)miss, l);
             uint64_t al = __shfl_sync(0xffffffffu, (unsigned long long)acc, l);
-            const int vl = (int)(w * 32 + l);
             for (int b2 = jl; b2 < el && al != ml; b2 += 32) {
                 const int idx = b2 + (int)lane;
                 int uu = 0;
@@ -443,8 +451,7 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
                 while (gb) {  // warp-uniform: the first (lowest index) provider of each lane
                     const int bj = __ffsll((long long)gb) - 1;
                     const unsigned who = __ballot_sync(0xffffffffu, (fu >> bj) & 1ull);
-                    const int par = __shfl_sync(0xffffffffu, uu, __ffs(who) - 1);
-                    if (lane == 0 && sm.parent[bj]) sm.parent[bj][vl] = par;
+                    if (lane == 0) pidx[bj * 32 + l] = (unsigned short)(b2 + __ffs(who) - 1 - bl);
                     gb &= gb - 1;
                 }
                 al |= got;
@@ -452,12 +459,20 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             if ((int)lane == l) acc = al;
             rm &= rm - 1;
         }
+        // depths and parents of the word, lane-major: for each lane found
+        // anywhere in the word, its row entries of the 32 vertices go out together
         uint64_t all = warp_or64(acc);
+        __syncwarp();
         while (all) {  // warp-uniform
             const int bj = __ffsll((long long)all) - 1;
-            if ((acc >> bj) & 1ull) sm.depth[bj][v] = dnext;
+            if ((acc >> bj) & 1ull) {
+                sm.depth[bj][v] = dnext;
+                int32_t* pp = sm.parent[bj];
+                if (pp) pp[v] = __ldg(g.csc_col + beg + pidx[bj * 32 + lane]);
+            }
             all &= all - 1;
         }
+        __syncwarp();
         if (acc) {
             ((unsigned long long*)L.f_next)[v] = acc;
             ((unsigned long long*)p.seen)[v] |= acc;
@@ -850,7 +865,8 @@ static bfs_status alloc_wsms(int32_t ncap, int64_t ucap, int32_t chunk, int32_t 
 
 static int coop_blocks_ms(int blocks_per_sm) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel<MS_T>, MS_T, 0);
+    cudaFuncSetAttribute(msbfs_kernel<MS_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MS_PIDX_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel<MS_T>, MS_T, MS_PIDX_BYTES);
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     return per_sm * num_sms();
@@ -906,7 +922,8 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.acc_long = w->acc_long;
     int blocks = coop_blocks_ms(o.blocks_per_sm);
     void* args[] = {(void*)&p};
-    BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, 0, st));
+    BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, MS_PIDX_BYTES,
+                                         st));
     return BFS_OK;
 }
 
