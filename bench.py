@@ -459,8 +459,11 @@ def main():
         if os.path.exists(args.policy_weights):
             pol = bg.Policy(np.load(args.policy_weights))
             lms, _ = time_single(bg.options(batch=0, policy=bg.BFS_POLICY_MLP, mlp=pol))
+            hms, _ = time_single(bg.options(batch=0))  # the heuristic on the same timer, for a like-for-like ratio
             extra["learned_single"] = {"gteps": edges / (lms * 1e-3) / 1e9, "ms_per_step": lms,
-                                       "speedup_vs_plain": ms_per_step / lms, "depth_equal_to_plain": same_depths()}
+                                       "speedup_vs_plain": ms_per_step / lms, "heuristic_same_timer_ms": hms,
+                                       "speedup_vs_heuristic_same_timer": hms / lms,
+                                       "depth_equal_to_plain": same_depths()}
             blms = time_batched(bg.options(batch=1, policy=bg.BFS_POLICY_MLP, mlp=pol))
             extra["batched_learned"] = {"gteps": edges / (blms * 1e-3) / 1e9, "ms_per_step": blms,
                                         "speedup_vs_plain": ms_per_step / blms, "depth_equal_to_plain": same_depths()}

@@ -110,7 +110,8 @@ enum {
     BFS_POLICY_PUSH = 1,      /* push every level (queue or bitmap by the gamma threshold) */
     BFS_POLICY_PULL = 2,      /* pull every level */
     BFS_POLICY_SCHEDULE = 3,  /* level i uses schedule[i % schedule_len] */
-    BFS_POLICY_MLP = 4        /* learned policy `mlp` (falls back to HEURISTIC when NULL) */
+    BFS_POLICY_MLP = 4        /* learned policy `mlp` where the HEURISTIC's test is close (1/8 < e_f*alpha/m_u < 8),
+                                 the HEURISTIC elsewhere and when `mlp` is NULL */
 };
 
 /* One record per executed level, written when bfs_options.level_log != NULL. */
@@ -225,7 +226,9 @@ bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int
 /*
  * Direction policy: an FP32 MLP 10 -> 32 -> 32 -> 3 (ReLU) whose argmax picks
  * BFS_DIR_*.  The paper has no learned policy; it replaces the Beamer switch
- * it cites (Section 5).  Parameter layout (1507 floats, row-major):
+ * it cites (Section 5) where that switch's own test is close -- e_f * alpha /
+ * m_u within (1/8, 8) -- and the heuristic decides the clear-cut levels (and
+ * costs no network evaluation there).  Parameter layout (1507 floats, row-major):
  *   W1[32][10] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]
  * followed by 20 floats of input normalisation: mean[10], inv_std[10].
  */
@@ -278,6 +281,18 @@ bfs_status bfs_policy_forward(const bfs_policy* p, const float* X, int64_t rows,
  */
 bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const int32_t* y, int64_t rows, float lr,
                                  int32_t step, float* loss_out, float* grad_out, void* cuda_stream);
+
+/*
+ * The same step on a least-squares objective: L = (1/R) sum_r sum_c
+ * (z_rc - target_rc)^2 / 2 over the raw outputs z (no softmax), target device
+ * float [rows][3] row-major; dL/dz = (z - target) / R.  Trained on
+ * -log(T_c / T_min) of profiled levels, the outputs estimate how much slower
+ * each traversal form is, and their argmax -- the form the search takes -- is
+ * the one predicted fastest.  Other arguments and errors as
+ * bfs_policy_train_step.
+ */
+bfs_status bfs_policy_train_step_regress(bfs_policy* p, const float* X, const float* target, int64_t rows, float lr,
+                                         int32_t step, float* loss_out, float* grad_out, void* cuda_stream);
 
 /* Replace the normalisation (mean[10], inv_std[10], host) used by forward/train. */
 bfs_status bfs_policy_set_norm(bfs_policy* p, const float* mean_inv_std);

@@ -69,6 +69,8 @@ def _load():
         lib.or_mlp_forward.restype = ctypes.c_int
         lib.or_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp]
         lib.or_mlp_loss_grad.restype = ctypes.c_int
+        lib.or_mlp_regress_loss_grad.argtypes = [vp, vp, vp, i64, vp, vp]
+        lib.or_mlp_regress_loss_grad.restype = ctypes.c_int
         lib.or_adam_step.argtypes = [vp, vp, vp, vp, i64, i64, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double]
         lib.or_adam_step.restype = ctypes.c_int
@@ -176,6 +178,18 @@ def mlp_loss_grad(params, X, y):
     loss = np.zeros(1, np.float64)
     grad = np.empty(mlp_num_params(), np.float64)
     _load().or_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(y), X.shape[0], _ptr(loss), _ptr(grad))
+    return float(loss[0]), grad
+
+
+def mlp_regress_loss_grad(params, X, t):
+    """Mean over rows of sum_j (z_j - t_j)^2 / 2 for the network outputs z, and its gradient."""
+    params = np.ascontiguousarray(params, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, N_IN)
+    t = np.ascontiguousarray(t, np.float64).reshape(-1, N_OUT)
+    assert t.shape[0] == X.shape[0]
+    loss = np.zeros(1, np.float64)
+    grad = np.empty(mlp_num_params(), np.float64)
+    _load().or_mlp_regress_loss_grad(_ptr(params), _ptr(X), _ptr(t), X.shape[0], _ptr(loss), _ptr(grad))
     return float(loss[0]), grad
 
 

@@ -333,53 +333,90 @@ int or_mlp_forward(const double* P, const double* X, int64_t rows, double* logit
 }
 
 /*
- * Mean softmax cross-entropy over rows, L = (1/R) sum_r [logsumexp(z_r) - z_r[y_r]],
- * and its gradient dL/dP by the chain rule written out layer by layer
- * (ReLU derivative taken as 0 at 0).  grad has OR_NPARAM entries.
+ * Add one row's contribution to dL/dP given dL/dz for that row: the chain rule
+ * written out layer by layer (ReLU derivative taken as 0 at 0).
  */
-int or_mlp_loss_grad(const double* P, const double* X, const int32_t* y, int64_t rows, double* loss,
-                     double* grad) {
+static void mlp_backprop_row(const double* P, const double* x, const double* h1, const double* h2, const double* dz,
+                             double* grad) {
     const double *W2 = P + OR_H * OR_IN + OR_H, *W3 = W2 + OR_H * OR_H + OR_H;
     double *gW1 = grad, *gb1 = gW1 + OR_H * OR_IN, *gW2 = gb1 + OR_H, *gb2 = gW2 + OR_H * OR_H;
     double *gW3 = gb2 + OR_H, *gb3 = gW3 + OR_OUT * OR_H;
+    double dh2[OR_H];
+    for (int k = 0; k < OR_H; ++k) dh2[k] = 0;
+    for (int j = 0; j < OR_OUT; ++j) {
+        gb3[j] += dz[j];
+        for (int k = 0; k < OR_H; ++k) {
+            gW3[j * OR_H + k] += dz[j] * h2[k];
+            dh2[k] += W3[j * OR_H + k] * dz[j];
+        }
+    }
+    double dh1[OR_H];
+    for (int k = 0; k < OR_H; ++k) dh1[k] = 0;
+    for (int j = 0; j < OR_H; ++j) {
+        double da = h2[j] > 0 ? dh2[j] : 0;
+        gb2[j] += da;
+        for (int k = 0; k < OR_H; ++k) {
+            gW2[j * OR_H + k] += da * h1[k];
+            dh1[k] += W2[j * OR_H + k] * da;
+        }
+    }
+    for (int j = 0; j < OR_H; ++j) {
+        double da = h1[j] > 0 ? dh1[j] : 0;
+        gb1[j] += da;
+        for (int k = 0; k < OR_IN; ++k) gW1[j * OR_IN + k] += da * x[k];
+    }
+}
+
+/* log(sum_j exp(z_j)) of one row of logits, shifted by the largest logit. */
+static double logsumexp_row(const double* z) {
+    double zmax = z[0];
+    for (int j = 1; j < OR_OUT; ++j) zmax = z[j] > zmax ? z[j] : zmax;
+    double se = 0;
+    for (int j = 0; j < OR_OUT; ++j) se += exp(z[j] - zmax);
+    return zmax + log(se);
+}
+
+/*
+ * Mean softmax cross-entropy over rows, L = (1/R) sum_r [logsumexp(z_r) - z_r[y_r]],
+ * and its gradient dL/dP.  grad has OR_NPARAM entries.
+ */
+int or_mlp_loss_grad(const double* P, const double* X, const int32_t* y, int64_t rows, double* loss,
+                     double* grad) {
     memset(grad, 0, sizeof(double) * OR_NPARAM);
     double total = 0;
     for (int64_t r = 0; r < rows; ++r) {
         const double* x = X + r * OR_IN;
         double h1[OR_H], h2[OR_H], z[OR_OUT];
         mlp_forward_row(P, x, h1, h2, z);
-        double zmax = z[0];
-        for (int j = 1; j < OR_OUT; ++j) zmax = z[j] > zmax ? z[j] : zmax;
-        double se = 0;
-        for (int j = 0; j < OR_OUT; ++j) se += exp(z[j] - zmax);
-        double lse = zmax + log(se);
+        const double lse = logsumexp_row(z);
         total += lse - z[y[r]];
         double dz[OR_OUT];
         for (int j = 0; j < OR_OUT; ++j) dz[j] = (exp(z[j] - lse) - (j == y[r] ? 1.0 : 0.0)) / (double)rows;
-        double dh2[OR_H];
-        for (int k = 0; k < OR_H; ++k) dh2[k] = 0;
+        mlp_backprop_row(P, x, h1, h2, dz, grad);
+    }
+    *loss = total / (double)rows;
+    return 0;
+}
+
+/*
+ * Least-squares regression of the outputs on per-row targets,
+ * L = (1/R) sum_r sum_j (z_rj - t_rj)^2 / 2, and dL/dP; dL/dz_rj = (z_rj - t_rj) / R.
+ * grad has OR_NPARAM entries.
+ */
+int or_mlp_regress_loss_grad(const double* P, const double* X, const double* t, int64_t rows, double* loss,
+                             double* grad) {
+    memset(grad, 0, sizeof(double) * OR_NPARAM);
+    double total = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const double* x = X + r * OR_IN;
+        const double* tr = t + r * OR_OUT;
+        double h1[OR_H], h2[OR_H], z[OR_OUT], dz[OR_OUT];
+        mlp_forward_row(P, x, h1, h2, z);
         for (int j = 0; j < OR_OUT; ++j) {
-            gb3[j] += dz[j];
-            for (int k = 0; k < OR_H; ++k) {
-                gW3[j * OR_H + k] += dz[j] * h2[k];
-                dh2[k] += W3[j * OR_H + k] * dz[j];
-            }
+            total += 0.5 * (z[j] - tr[j]) * (z[j] - tr[j]);
+            dz[j] = (z[j] - tr[j]) / (double)rows;
         }
-        double dh1[OR_H];
-        for (int k = 0; k < OR_H; ++k) dh1[k] = 0;
-        for (int j = 0; j < OR_H; ++j) {
-            double da = h2[j] > 0 ? dh2[j] : 0;
-            gb2[j] += da;
-            for (int k = 0; k < OR_H; ++k) {
-                gW2[j * OR_H + k] += da * h1[k];
-                dh1[k] += W2[j * OR_H + k] * da;
-            }
-        }
-        for (int j = 0; j < OR_H; ++j) {
-            double da = h1[j] > 0 ? dh1[j] : 0;
-            gb1[j] += da;
-            for (int k = 0; k < OR_IN; ++k) gW1[j * OR_IN + k] += da * x[k];
-        }
+        mlp_backprop_row(P, x, h1, h2, dz, grad);
     }
     *loss = total / (double)rows;
     return 0;

@@ -38,6 +38,7 @@ EXPORTED = [
     "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_level_stats_noalloc", "bfs_profile_levels",
     "bfs_policy_features", "bfs_policy_load",
     "bfs_policy_weights", "bfs_policy_free", "bfs_policy_forward", "bfs_policy_train_step",
+    "bfs_policy_train_step_regress",
     "bfs_policy_set_norm", "bfs_status_string", "bfs_last_error", "bfs_version",
 ]
 
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
         "bfs_policy_free": (None, [vp]),
         "bfs_policy_forward": (st, [vp, vp, i64, vp, vp]),
         "bfs_policy_train_step": (st, [vp, vp, vp, i64, ctypes.c_float, i32, vp, vp, vp]),
+        "bfs_policy_train_step_regress": (st, [vp, vp, vp, i64, ctypes.c_float, i32, vp, vp, vp]),
         "bfs_policy_set_norm": (st, [vp, vp]),
         "bfs_status_string": (ctypes.c_char_p, [st]),
         "bfs_last_error": (ctypes.c_char_p, []),
@@ -296,6 +298,13 @@ class Policy:
         loss = np.zeros(1, np.float32)
         _check(load().bfs_policy_train_step(self.handle, _ptr(X), _ptr(y), int(rows), float(lr), int(step),
                                             _ptr(loss), _ptr(grad_out), _stream(stream)))
+        return float(loss[0])
+
+    def train_step_regress(self, X, target, rows: int, lr: float, step: int, grad_out=None, stream=None) -> float:
+        """One Adam step of least-squares regression of the outputs on target (device float [rows][3])."""
+        loss = np.zeros(1, np.float32)
+        _check(load().bfs_policy_train_step_regress(self.handle, _ptr(X), _ptr(target), int(rows), float(lr),
+                                                    int(step), _ptr(loss), _ptr(grad_out), _stream(stream)))
         return float(loss[0])
 
     def free(self):

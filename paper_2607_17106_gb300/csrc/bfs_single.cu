@@ -65,12 +65,23 @@ void free_ws1(Workspace1* w) {
 
 
 // ------------------------------------------------------------ the kernel
+// Dynamic shared memory of the persistent kernel: a copy of the policy
+// weights, evaluated by every CTA at every level when the policy is the MLP.
+constexpr size_t BFS1_DYN_SMEM = (size_t)NWEIGHTS * sizeof(float);
+extern __shared__ float bfs1_dyn_smem[];
+
 template <int T>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
     __shared__ PullWarpSmem s_pull[T / 32];
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
+    const float* mlp_w = nullptr;
+    if (p.policy == BFS_POLICY_MLP && p.mlp) {
+        for (int i = threadIdx.x; i < NWEIGHTS; i += T) bfs1_dyn_smem[i] = __ldg(p.mlp + i);
+        __syncthreads();
+        mlp_w = bfs1_dyn_smem;
+    }
     Ctl1* ctl = p.ctl;
     const unsigned nblocks = gridDim.x;
     const long long gtid = (long long)blockIdx.x * T + threadIdx.x;
@@ -134,7 +145,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             break;
         }
         if (level > 0) m_u -= e_f;
-        int dir = decide_dir(p, level, f, e_f, m_u, f_prev, prev_dir, s_feat, &s_mlp_out);
+        int dir = decide_dir(p, level, f, e_f, m_u, f_prev, prev_dir, s_feat, &s_mlp_out, mlp_w);
         if (gtid == 0 && p.log && level < p.log_cap) {
             bfs_level_record r;
             r.level = level;
@@ -251,13 +262,14 @@ struct LaunchCfg {
 template <int T>
 cudaError_t launch_bfs1(const Params1& p, int blocks, cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel((const void*)bfs1_kernel<T>, dim3(blocks), dim3(T), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)bfs1_kernel<T>, dim3(blocks), dim3(T), args, BFS1_DYN_SMEM, st);
 }
 
 template <int T>
 int max_coop_blocks(int blocks_per_sm) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T>, T, 0);
+    cudaFuncSetAttribute(bfs1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T>, T, BFS1_DYN_SMEM);
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     return per_sm * num_sms();

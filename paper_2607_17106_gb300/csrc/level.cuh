@@ -105,13 +105,31 @@ struct Params1 {
 };
 
 // ------------------------------------------------------------- direction
+// Direction tests use FP32: every thread of every CTA evaluates them at every
+// level, and GB300's FP64 rate is a small fraction of its FP32 rate (a
+// double division per thread per level measurably lengthened each level).
 __device__ __forceinline__ int push_kind(const Params1& p, long long f) {
-    return ((double)f * p.gamma > (double)p.n) ? BFS_DIR_PUSH_BITMAP : BFS_DIR_PUSH_QUEUE;
+    return ((float)f * p.gamma > (float)p.n) ? BFS_DIR_PUSH_BITMAP : BFS_DIR_PUSH_QUEUE;
+}
+
+// Beamer et al. 2012 (cited in Section 5): top-down while the frontier's
+// edges are few relative to the unexplored edges; bottom-up while the
+// frontier is growing or large.
+__device__ __forceinline__ int heuristic_dir(const Params1& p, long long f, long long e_f, long long m_u,
+                                             long long f_prev, int prev_dir) {
+    if (prev_dir == BFS_DIR_PULL) {
+        bool stay = (f >= f_prev) || ((float)f * p.beta > (float)p.n);
+        return stay ? BFS_DIR_PULL : push_kind(p, f);
+    }
+    if ((float)e_f * p.alpha > (float)m_u && f > f_prev) return BFS_DIR_PULL;
+    return push_kind(p, f);
 }
 
 // Same inputs on every CTA -> same decision (all arithmetic is deterministic).
+// mlp_w: the policy weights to evaluate (a shared-memory copy when the
+// caller staged one), else p.mlp.  Block-uniform.
 __device__ inline int decide_dir(const Params1& p, int level, long long f, long long e_f, long long m_u, long long f_prev,
-                          int prev_dir, float* s_feat, float* s_mlp_out) {
+                          int prev_dir, float* s_feat, float* s_mlp_out, const float* mlp_w = nullptr) {
     if (p.force_dir >= 0) return p.force_dir;
     switch (p.policy) {
         case BFS_POLICY_PUSH:
@@ -123,13 +141,13 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
             return (d < 0 || d > 2) ? BFS_DIR_PUSH_QUEUE : d;
         }
         case BFS_POLICY_MLP:
-            if (p.mlp) {
+            if (p.mlp && policy_in_band(e_f, m_u, p.alpha)) {
                 // warp 0 evaluates; result broadcast through shared memory
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
                         policy_features(s_feat, f, e_f, m_u, f_prev, level, prev_dir, p.n, p.m, p.deg_max);
                     __syncwarp();
-                    int a = policy_argmax_warp(p.mlp, s_feat);
+                    int a = policy_argmax_warp(mlp_w ? mlp_w : p.mlp, s_feat);
                     if (threadIdx.x == 0) *s_mlp_out = (float)a;
                 }
                 __syncthreads();
@@ -137,18 +155,9 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
                 __syncthreads();
                 return a;
             }
-            // fall through to the heuristic
-        default: {
-            // Beamer et al. 2012 (cited in Section 5): top-down while the
-            // frontier's edges are few relative to the unexplored edges;
-            // bottom-up while the frontier is growing or large.
-            if (prev_dir == BFS_DIR_PULL) {
-                bool stay = (f >= f_prev) || ((double)f * p.beta > (double)p.n);
-                return stay ? BFS_DIR_PULL : push_kind(p, f);
-            }
-            if ((double)e_f * p.alpha > (double)m_u && f > f_prev) return BFS_DIR_PULL;
-            return push_kind(p, f);
-        }
+            return heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
+        default:
+            return heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
     }
 }
 

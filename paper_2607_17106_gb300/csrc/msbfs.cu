@@ -595,7 +595,7 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
             d = p.schedule[level % p.schedule_len];
             return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
         case BFS_POLICY_MLP:
-            if (p.mlp) {
+            if (p.mlp && policy_in_band(e_f, m_u, p.alpha)) {
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
                         policy_features(sm.feat, a, e_f, m_u, a_prev, level, prev_dir, g.n, g.m, deg_max);
@@ -608,13 +608,13 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
                 __syncthreads();
                 return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
             }
-            // no weights: fall through to the heuristic
+            // no weights, or a clear-cut level: the heuristic decides
         default:
             if (prev_dir == BFS_DIR_PULL) {
-                bool stay = (a >= a_prev) || ((double)a * p.beta > (double)g.n);
+                bool stay = (a >= a_prev) || ((float)a * p.beta > (float)g.n);
                 return stay ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
             }
-            if ((double)e_f * p.alpha > (double)m_u && a > a_prev) return BFS_DIR_PULL;
+            if ((float)e_f * p.alpha > (float)m_u && a > a_prev) return BFS_DIR_PULL;
             return BFS_DIR_PUSH_QUEUE;
     }
 }

@@ -1,6 +1,7 @@
 // policy.cu -- learned push/pull direction policy: FP32 MLP 10 -> 32 -> 32 -> 3
-// (ReLU) with its forward, softmax cross-entropy backward and Adam update in
-// this library's own kernels.  The paper has no learned policy; it stands in
+// (ReLU) with its forward, backward (softmax cross-entropy on labels, or
+// least-squares regression of the outputs on per-row targets) and Adam update
+// in this library's own kernels.  The paper has no learned policy; it stands in
 // for the Beamer direction switch the paper cites (Section 5).
 #include "common.cuh"
 #include "policy_dev.cuh"
@@ -63,10 +64,13 @@ __global__ void mlp_forward_kernel(const float* w, const float* X, int64_t rows,
     }
 }
 
-// Per row: forward, dL/dz of the mean cross-entropy, and the back-propagated
-// pre-activation gradients of both hidden layers (stored for the reductions).
-__global__ void mlp_backward_rows_kernel(const float* w, const float* X, const int32_t* y, int64_t rows, float* scratch,
-                                         float* loss) {
+// Per row: forward, dL/dz, and the back-propagated pre-activation gradients
+// of both hidden layers (stored for the reductions).  REGRESS = false: mean
+// softmax cross-entropy on the labels y.  REGRESS = true: mean of
+// sum_c (z_c - t_c)^2 / 2 on the row's targets t (3 floats), dL/dz = z - t.
+template <bool REGRESS>
+__global__ void mlp_backward_rows_kernel(const float* w, const float* X, const int32_t* y, const float* t,
+                                         int64_t rows, float* scratch, float* loss) {
     __shared__ float sw[NWEIGHTS];
     load_weights(sw, w);
     float lsum = 0.0f;
@@ -75,14 +79,23 @@ __global__ void mlp_backward_rows_kernel(const float* w, const float* X, const i
         float* s = scratch + r * ROW_STRIDE;
         float xn[MLP_IN], h1[MLP_H], h2[MLP_H], z[MLP_OUT];
         forward_row(sw, X + r * MLP_IN, xn, h1, h2, z);
-        float zmax = fmaxf(z[0], fmaxf(z[1], z[2]));
-        float se = 0.0f;
-        for (int c = 0; c < MLP_OUT; ++c) se += expf(z[c] - zmax);
-        float lse = zmax + logf(se);
-        int yr = y[r];
-        lsum += lse - z[yr];
         float dz[MLP_OUT];
-        for (int c = 0; c < MLP_OUT; ++c) dz[c] = (expf(z[c] - lse) - (c == yr ? 1.0f : 0.0f)) * inv_rows;
+        if (REGRESS) {
+            const float* tr = t + r * MLP_OUT;
+            for (int c = 0; c < MLP_OUT; ++c) {
+                const float e = z[c] - tr[c];
+                lsum = fmaf(0.5f * e, e, lsum);
+                dz[c] = e * inv_rows;
+            }
+        } else {
+            float zmax = fmaxf(z[0], fmaxf(z[1], z[2]));
+            float se = 0.0f;
+            for (int c = 0; c < MLP_OUT; ++c) se += expf(z[c] - zmax);
+            float lse = zmax + logf(se);
+            int yr = y[r];
+            lsum += lse - z[yr];
+            for (int c = 0; c < MLP_OUT; ++c) dz[c] = (expf(z[c] - lse) - (c == yr ? 1.0f : 0.0f)) * inv_rows;
+        }
         float da2[MLP_H];
         for (int j = 0; j < MLP_H; ++j) {
             float d = 0.0f;
@@ -207,13 +220,14 @@ extern "C" bfs_status bfs_policy_forward(const bfs_policy* p, const float* X, in
     return BFS_OK;
 }
 
-extern "C" bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const int32_t* y, int64_t rows, float lr,
-                                            int32_t step, float* loss_out, float* grad_out, void* cuda_stream) {
-    if (!p || !X || !y) return fail(BFS_EINVAL, "null argument");
+namespace {
+
+// One training step on either objective: gradient into p->grad (optionally
+// copied out), Adam update of the parameters, mean loss optionally read back.
+bfs_status train_step(bfs_policy* p, const float* X, const int32_t* y, const float* t, int64_t rows, float lr,
+                      int32_t step, float* loss_out, float* grad_out, cudaStream_t st) {
     if (rows <= 0 || step < 1) return fail(BFS_EINVAL, "rows must be > 0 and step >= 1");
-    if (!is_device_ptr(X) || !is_device_ptr(y)) return fail(BFS_EINVAL, "X and y must be device memory");
     if (rows > (int64_t)512 * 65535) return fail(BFS_ERANGE, "at most %lld rows per step", (long long)512 * 65535);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     if (p->scratch_rows < rows) {
         BFS_CUDA(cudaStreamSynchronize(st));
         cudaFree(p->scratch);
@@ -228,7 +242,8 @@ extern "C" bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const
     BFS_CUDA(cudaMemsetAsync(p->loss, 0, 4, st));
     BFS_CUDA(cudaMemsetAsync(p->grad, 0, NPARAM * 4, st));
     int blocks = (int)std::min<int64_t>(div_up(rows, 128), (int64_t)num_sms() * 8);
-    mlp_backward_rows_kernel<<<blocks, 128, 0, st>>>(p->w, X, y, rows, p->scratch, p->loss);
+    if (t) mlp_backward_rows_kernel<true><<<blocks, 128, 0, st>>>(p->w, X, nullptr, t, rows, p->scratch, p->loss);
+    else mlp_backward_rows_kernel<false><<<blocks, 128, 0, st>>>(p->w, X, y, nullptr, rows, p->scratch, p->loss);
     const int rpc = 512;
     dim3 g((NPARAM + 255) / 256, (unsigned)div_up(rows, rpc));
     mlp_grad_reduce_kernel<<<g, 256, 0, st>>>(p->scratch, rows, rpc, p->grad);
@@ -242,6 +257,23 @@ extern "C" bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const
         BFS_CUDA(cudaStreamSynchronize(st));
     }
     return BFS_OK;
+}
+
+}  // namespace
+
+extern "C" bfs_status bfs_policy_train_step(bfs_policy* p, const float* X, const int32_t* y, int64_t rows, float lr,
+                                            int32_t step, float* loss_out, float* grad_out, void* cuda_stream) {
+    if (!p || !X || !y) return fail(BFS_EINVAL, "null argument");
+    if (!is_device_ptr(X) || !is_device_ptr(y)) return fail(BFS_EINVAL, "X and y must be device memory");
+    return train_step(p, X, y, nullptr, rows, lr, step, loss_out, grad_out, (cudaStream_t)cuda_stream);
+}
+
+extern "C" bfs_status bfs_policy_train_step_regress(bfs_policy* p, const float* X, const float* target, int64_t rows,
+                                                    float lr, int32_t step, float* loss_out, float* grad_out,
+                                                    void* cuda_stream) {
+    if (!p || !X || !target) return fail(BFS_EINVAL, "null argument");
+    if (!is_device_ptr(X) || !is_device_ptr(target)) return fail(BFS_EINVAL, "X and target must be device memory");
+    return train_step(p, X, nullptr, target, rows, lr, step, loss_out, grad_out, (cudaStream_t)cuda_stream);
 }
 
 extern "C" bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,

@@ -50,9 +50,22 @@ __host__ __device__ inline void policy_features(float* x, long long f, long long
     x[9] = log2f(nn) / 32.0f;
 }
 
+// The learned policy is consulted only where the heuristic's own test is
+// close -- e_f * alpha / m_u within (1/MLP_TRUST, MLP_TRUST) -- the levels
+// where the right form depends on more than that ratio; elsewhere the
+// heuristic decides, which also keeps the network away from the clear-cut
+// levels where a wrong form is slower by orders of magnitude.
+constexpr float MLP_TRUST = 8.0f;
+__host__ __device__ inline bool policy_in_band(long long e_f, long long m_u, float alpha) {
+    const float a = (float)(e_f > 1 ? e_f : 1) * alpha, b = (float)(m_u > 1 ? m_u : 1);  // ratio a / b, FP32, no division
+    return a * MLP_TRUST > b && a < b * MLP_TRUST;
+}
+
 #ifdef __CUDACC__
 // Warp-cooperative forward pass (lane j owns hidden unit j); returns the
 // argmax class (lowest index on ties) on every lane.  x: 10 raw features.
+// Lane j visits the 32 terms of its second-layer row starting at term j, so
+// that with w in shared memory the lanes read 32 different banks.
 __device__ inline int policy_argmax_warp(const float* __restrict__ w, const float* x) {
     const unsigned lane = threadIdx.x & 31;
     float xn[MLP_IN];
@@ -64,7 +77,10 @@ __device__ inline int policy_argmax_warp(const float* __restrict__ w, const floa
     h1 = fmaxf(h1, 0.0f);
     float h2 = w[OFF_B2 + lane];
 #pragma unroll 8
-    for (int k = 0; k < MLP_H; ++k) h2 = fmaf(w[OFF_W2 + lane * MLP_H + k], __shfl_sync(0xffffffffu, h1, k), h2);
+    for (int k = 0; k < MLP_H; ++k) {
+        const int kk = (k + (int)lane) & (MLP_H - 1);
+        h2 = fmaf(w[OFF_W2 + lane * MLP_H + kk], __shfl_sync(0xffffffffu, h1, kk), h2);
+    }
     h2 = fmaxf(h2, 0.0f);
     float z[MLP_OUT];
 #pragma unroll

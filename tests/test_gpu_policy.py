@@ -83,6 +83,48 @@ def test_gradient_and_adam_step_match_fp64_reference():
     assert np.max(np.abs(w - Pn)) <= 1e-6 + 1e-5 * lr
 
 
+def test_regression_gradient_and_adam_step_match_fp64_reference():
+    P = _params(15).astype(np.float32).astype(np.float64)
+    pol = bg.Policy(_identity_norm_weights(P))
+    rng = np.random.default_rng(16)
+    rows = 2500
+    X = rng.normal(0, 1, (rows, 10)).astype(np.float32)
+    t = -rng.exponential(1.0, (rows, 3)).astype(np.float32)
+    loss_ref, g_ref = oracle.mlp_regress_loss_grad(P, X.astype(np.float64), t.astype(np.float64))
+    grad = torch.empty(bg.BFS_MLP_NPARAM, dtype=torch.float32, device="cuda")
+    lr = 1e-2
+    loss = pol.train_step_regress(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), rows, lr, 1, grad_out=grad)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref)) <= 1e-4
+    assert abs(loss - loss_ref) / loss_ref <= 1e-5
+    Pn = P.copy()
+    m1, m2 = np.zeros_like(P), np.zeros_like(P)
+    oracle.adam_step(Pn, m1, m2, g, t=1, lr=lr, eps=1e-8)
+    w = pol.weights().astype(np.float64)[: bg.BFS_MLP_NPARAM]
+    assert np.max(np.abs(w - Pn)) <= 1e-6 + 1e-5 * lr
+
+
+def test_regression_training_fits_smooth_targets():
+    # targets that are smooth functions of the features: the loss must fall
+    # well below its start, and the argmax of the fit picks the largest target
+    rng = np.random.default_rng(17)
+    rows = 2048
+    X = rng.normal(0, 1, (rows, 10)).astype(np.float32)
+    t = np.stack([-np.maximum(X[:, 0], 0), -np.maximum(-X[:, 0], 0), -0.5 + 0 * X[:, 0]], axis=1).astype(np.float32)
+    pol = bg.Policy(_identity_norm_weights(_params(18) * 0.5))
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    first = pol.train_step_regress(Xd, td, rows, 1e-2, 1)
+    last = first
+    for k in range(2, 401):
+        last = pol.train_step_regress(Xd, td, rows, 1e-2, k)
+    assert last < 0.05 * first
+    out = torch.empty(rows, 3, dtype=torch.float32, device="cuda")
+    pol.forward(Xd, out, rows)
+    pick = out.argmax(1).cpu().numpy()
+    assert -t[np.arange(rows), pick].mean() < -t.max(axis=1).mean() + 0.05
+
+
 def test_training_reduces_loss_on_a_separable_task():
     rng = np.random.default_rng(7)
     rows = 2048
@@ -139,10 +181,16 @@ def test_policy_pipeline_trains_and_drives_searches():
     specs = pl.training_specs(6, 12, 14, seed=77)
     X, T, K, G = pl.collect(specs, sources_per_graph=2, repeats=1)
     y = T.argmin(axis=1).astype(np.int32)
-    pol = pl.fit(X, y, epochs=300, lr=3e-3)
-    assert np.isfinite(pol.final_loss)
+    pol_ce = pl.fit(X, y, epochs=300, lr=3e-3)
+    assert np.isfinite(pol_ce.final_loss)
+    assert pl.predict(pol_ce, X).shape == y.shape
+    # the log-time regression: on the levels it was trained on, the
+    # network's choices cost no more time than the heuristic's (K)
+    pol = pl.fit(X, None, epochs=600, lr=3e-3, target=pl.log_time_targets(T))
     choice = pl.predict(pol, X)
     assert choice.shape == y.shape
+    r_mlp, r_heur = pl.regret(pl.gate(choice, X, K), T), pl.regret(K, T)
+    assert r_mlp["time_us"] <= r_heur["time_us"] * 1.02, (r_mlp, r_heur)
     import graphgen
     n, s, d = graphgen.rmat(13, 16, seed=5)
     adj = oracle.build_adjacency(n, s, d)

@@ -6,6 +6,7 @@
 - validator: accepts oracle output, rejects each kind of corrupted parent/depth
 - per-level statistics: closed forms on path and complete graphs, identities of Cascade 1
 - MLP FP64 reference: central finite differences, zero-parameter closed form, Adam step 1
+- regression loss: finite differences, constant-output closed form, exact-fit zero
 """
 import itertools
 
@@ -277,6 +278,41 @@ def test_mlp_closed_forms():
     X = np.zeros((3, oracle.N_IN)); X[:, 0] = [1.5, -2.0, 0.0]
     Z = oracle.mlp_forward(P, X)
     assert np.allclose(Z, np.outer(np.maximum(X[:, 0], 0), c))
+
+
+def test_mlp_regression_gradient_matches_central_finite_differences():
+    rng = np.random.default_rng(5)
+    P = _random_params(6)
+    X = rng.normal(0, 1, (13, oracle.N_IN))
+    t = rng.normal(0, 2, (13, oracle.N_OUT))
+    loss, g = oracle.mlp_regress_loss_grad(P, X, t)
+    h = 1e-6
+    num = np.empty_like(g)
+    for i in range(len(P)):
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        num[i] = (oracle.mlp_regress_loss_grad(Pp, X, t)[0] - oracle.mlp_regress_loss_grad(Pm, X, t)[0]) / (2 * h)
+    assert np.max(np.abs(num - g)) / np.max(np.abs(g)) < 1e-7
+    assert loss > 0
+
+
+def test_mlp_regression_closed_forms():
+    rng = np.random.default_rng(8)
+    X = rng.normal(0, 1, (6, oracle.N_IN))
+    t = rng.uniform(-5, 0, (6, oracle.N_OUT))
+    # only the output bias set: z = b3 for every row, so L = mean |b3 - t|^2 / 2
+    # and dL/db3 = b3 - mean(t); nothing reaches the zero weights
+    P = np.zeros(oracle.mlp_num_params())
+    b3 = np.array([0.5, -1.0, 2.0])
+    P[-3:] = b3
+    loss, g = oracle.mlp_regress_loss_grad(P, X, t)
+    assert abs(loss - 0.5 * ((b3 - t) ** 2).sum(axis=1).mean()) < 1e-13
+    assert np.allclose(g[-3:], b3 - t.mean(axis=0), atol=1e-14)
+    assert np.all(g[:-3] == 0)
+    # targets equal to the network's own outputs: zero loss, zero gradient
+    P = _random_params(9)
+    loss, g = oracle.mlp_regress_loss_grad(P, X, oracle.mlp_forward(P, X))
+    assert loss < 1e-28 and np.max(np.abs(g)) < 1e-14
 
 
 def test_adam_first_step_is_lr_times_sign():
