@@ -154,6 +154,7 @@ constexpr int MS_LONG_ITEMS = 4;  // entries a thread tests per long-row chunk
 #define BFS_MS_PULL_R 4
 #endif
 constexpr int MS_PULL_R = BFS_MS_PULL_R;  // in-neighbours loaded per serial pull step
+constexpr int MS_COOP_U = 4;  // 32-entry groups a warp loads per step when it finishes a long row
 
 struct MsSmem {
     int32_t* depth[64];
@@ -438,20 +439,33 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             const int bl = __shfl_sync(0xffffffffu, beg, l);
             const uint64_t ml = __shfl_sync(0xffffffffu, (unsigned long long)miss, l);
             uint64_t al = __shfl_sync(0xffffffffu, (unsigned long long)acc, l);
-            for (int b2 = jl; b2 < el && al != ml; b2 += 32) {
-                const int idx = b2 + (int)lane;
-                int uu = 0;
-                uint64_t fu = 0;
-                if (idx < el) {
-                    uu = __ldg(g.csc_col + idx);
-                    fu = F[uu] & ml & ~al;
+            // MS_COOP_U * 32 entries a step: all column loads, then all mask loads
+            for (int b2 = jl; b2 < el && al != ml; b2 += 32 * MS_COOP_U) {
+                int uu[MS_COOP_U];
+                uint64_t fu[MS_COOP_U];
+#pragma unroll
+                for (int q = 0; q < MS_COOP_U; ++q) {
+                    const int idx = b2 + q * 32 + (int)lane;
+                    uu[q] = idx < el ? __ldg(g.csc_col + idx) : -1;
                 }
-                const uint64_t got = warp_or64(fu);
+                uint64_t mine = 0;
+#pragma unroll
+                for (int q = 0; q < MS_COOP_U; ++q) {
+                    fu[q] = uu[q] >= 0 ? (F[uu[q]] & ml & ~al) : 0ull;
+                    mine |= fu[q];
+                }
+                const uint64_t got = warp_or64(mine);
                 uint64_t gb = got;
                 while (gb) {  // warp-uniform: the first (lowest index) provider of each lane
                     const int bj = __ffsll((long long)gb) - 1;
-                    const unsigned who = __ballot_sync(0xffffffffu, (fu >> bj) & 1ull);
-                    if (lane == 0) pidx[bj * 32 + l] = (unsigned short)(b2 + __ffs(who) - 1 - bl);
+#pragma unroll
+                    for (int q = 0; q < MS_COOP_U; ++q) {
+                        const unsigned who = __ballot_sync(0xffffffffu, (fu[q] >> bj) & 1ull);
+                        if (who) {
+                            if (lane == 0) pidx[bj * 32 + l] = (unsigned short)(b2 + q * 32 + __ffs(who) - 1 - bl);
+                            break;
+                        }
+                    }
                     gb &= gb - 1;
                 }
                 al |= got;
