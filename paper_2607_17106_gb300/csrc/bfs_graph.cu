@@ -146,18 +146,47 @@ __global__ void g_decide(Params1 p, cudaGraphConditionalHandle h_while, cudaGrap
     }
 }
 
+// What a level kernel needs from the control block, read by thread 0 and
+// shared with the CTA: every thread of every CTA reading the same words put
+// thousands of requests on one L2 sector (see cta_load_u64).
+struct GHead {
+    int level, units_valid;
+    long long f, nunits, m_u;
+    int32_t* depth;
+    int32_t* parent;
+};
+
+__device__ __forceinline__ GHead cta_head(const Ctl1* ctl) {
+    __shared__ GHead s;
+    if (threadIdx.x == 0) {
+        GHead h;
+        h.level = ctl->cur_level;
+        const Counters* c = &ctl->slot[h.level % 3];
+        h.f = (long long)c->q_len;
+        h.nunits = (long long)c->u_len;
+        h.m_u = ctl->m_u;
+        h.units_valid = ctl->units_valid;
+        h.depth = ctl->depth;
+        h.parent = ctl->parent;
+        s = h;
+    }
+    __syncthreads();
+    return s;
+}
+
 __global__ void __launch_bounds__(256) g_q2bm_zero(Params1 p) {
-    const int level = p.ctl->cur_level;
+    const int level = cta_head(p.ctl).level;
     uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < p.W; w += (long long)gridDim.x * blockDim.x)
         f_cur[w] = 0;
 }
 
 __global__ void __launch_bounds__(256) g_q2bm_scatter(Params1 p) {
-    const int level = p.ctl->cur_level;
+    const GHead h = cta_head(p.ctl);
+    const int level = h.level;
     uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
-    const long long f = (long long)p.ctl->slot[level % 3].q_len;
+    const long long f = h.f;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < f; q += (long long)gridDim.x * blockDim.x) {
         int v = q_cur[q];
         atomicOr(f_cur + (v >> 5), 1u << (v & 31));
@@ -166,7 +195,7 @@ __global__ void __launch_bounds__(256) g_q2bm_scatter(Params1 p) {
 
 __global__ void __launch_bounds__(GT) g_bm2q(Params1 p) {
     __shared__ TileSmem<GT> sm;
-    const int level = p.ctl->cur_level;
+    const int level = cta_head(p.ctl).level;
     uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
     int2* u_cur = (level & 1) ? p.U1 : p.U0;
@@ -177,15 +206,15 @@ template <int DIR>
 __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     __shared__ TileSmem<GT> sm;
     Ctl1* ctl = p.ctl;
-    const int level = ctl->cur_level;
-    Counters* cur = &ctl->slot[level % 3];
+    const GHead h = cta_head(ctl);
+    const int level = h.level;
     Counters* nxt = &ctl->slot[(level + 1) % 3];
-    const long long f = (long long)cur->q_len;
-    const long long nunits = (long long)cur->u_len;
+    const long long f = h.f;
+    const long long nunits = h.nunits;
     LevelCtx L;
     L.level = level;
-    L.depth = ctl->depth;
-    L.parent = ctl->parent;
+    L.depth = h.depth;
+    L.parent = h.parent;
     L.q_next = (level & 1) ? p.Q0 : p.Q1;
     L.u_next = (level & 1) ? p.U0 : p.U1;
     L.next = nxt;
@@ -193,11 +222,11 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.cnt = 0;
     L.qbuf = sm.qbuf + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
-    L.precheck = push_precheck(ctl->m_u, p.m);
+    L.precheck = push_precheck(h.m_u, p.m);
     const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const int2* u_cur = (level & 1) ? p.U1 : p.U0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
-    push_level<GT>(p, L, sm, DIR, q_cur, u_cur, f_cur, f, nunits, ctl->units_valid != 0);
+    push_level<GT>(p, L, sm, DIR, q_cur, u_cur, f_cur, f, nunits, h.units_valid != 0);
     unsigned long long ef = warp_sum(L.ef);
     if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = ef;
     __syncthreads();
@@ -215,11 +244,12 @@ __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     __shared__ unsigned long long s_ef[PULL_T / 32], s_cn[PULL_T / 32];
     __shared__ PullWarpSmem s_pull[PULL_T / 32];
     Ctl1* ctl = p.ctl;
-    const int level = ctl->cur_level;
+    const GHead h = cta_head(ctl);
+    const int level = h.level;
     LevelCtx L;
     L.level = level;
-    L.depth = ctl->depth;
-    L.parent = ctl->parent;
+    L.depth = h.depth;
+    L.parent = h.parent;
     L.ef = 0;
     L.cnt = 0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;

@@ -132,9 +132,12 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
         Counters* nxt = &ctl->slot[(level + 1) % 3];
-        long long f = (long long)__ldcg(&cur->q_len);
-        long long nunits = (long long)__ldcg(&cur->u_len);
-        long long e_f = (long long)__ldcg(&cur->e_f);
+        const unsigned long long* const csrc[3] = {&cur->q_len, &cur->u_len, &cur->e_f};
+        unsigned long long cv[3];
+        cta_load_u64<3>(csrc, cv);
+        long long f = (long long)cv[0];
+        long long nunits = (long long)cv[1];
+        long long e_f = (long long)cv[2];
         if (f == 0) {
             done = true;
             break;
@@ -175,7 +178,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             // bitmap -> queue conversion of F_i (after pull levels)
             bitmap_to_queue<T>(p, sm, f_cur, q_cur, u_cur, cur);
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
-            nunits = (long long)__ldcg(&cur->u_len);
+            const unsigned long long* const usrc[1] = {&cur->u_len};
+            unsigned long long uv[1];
+            cta_load_u64<1>(usrc, uv);
+            nunits = (long long)uv[0];
             q_valid = level;
         }
         if (gtid == 0) {

@@ -83,6 +83,34 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// An L2 (cache-global) load the compiler keeps where it is written: a level's
+// counters are read with three of these in a row, so that all three are in
+// flight together instead of the later ones being sunk past the first test
+// and costing another round trip.
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// Control-block words a whole CTA needs (a level's counters): thread 0 loads
+// them, the CTA reads them from shared memory.  When every warp of every CTA
+// loaded the same words after a grid barrier, thousands of requests queued on
+// one L2 sector and each level took about a microsecond longer.
+// Block-uniform; both barriers are needed (the first keeps a previous call's
+// readers ahead of thread 0's writes).
+template <int N>
+__device__ __forceinline__ void cta_load_u64(const unsigned long long* const (&src)[N], unsigned long long (&dst)[N]) {
+    __shared__ unsigned long long s[N];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[i] = ld_cg_u64(src[i]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) dst[i] = s[i];
+}
+
 __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }

@@ -709,9 +709,12 @@ __device__ void msbfs_body(const ParamsMS& p) {
         for (int level = 0;; ++level) {
             CountersMS* cur = &ctl->slot[level % 3];
             CountersMS* nxt = &ctl->slot[(level + 1) % 3];
-            long long a = (long long)__ldcg(&cur->a_len);
-            long long e_f = (long long)__ldcg(&cur->e_f);
-            const uint64_t live = (uint64_t)__ldcg(&cur->lanes);
+            const unsigned long long* const csrc[4] = {&cur->a_len, &cur->e_f, &cur->lanes, &cur->u_len};
+            unsigned long long cv[4];
+            cta_load_u64<4>(csrc, cv);
+            long long a = (long long)cv[0];
+            long long e_f = (long long)cv[1];
+            const uint64_t live = (uint64_t)cv[2];
             if (a == 0) break;
             if (level >= p.max_levels) {
                 if (gtid == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
@@ -732,13 +735,17 @@ __device__ void msbfs_body(const ParamsMS& p) {
             int32_t* a_cur = (level & 1) ? p.A1 : p.A0;
             int2* u_cur = (level & 1) ? p.U1 : p.U0;
             uint64_t* f_cur = (level & 1) ? p.F1 : p.F0;
+            long long nunits = (long long)cv[3];
             if (dir != BFS_DIR_PULL && list_valid != level) {
-                // active list of a pull-made frontier
+                // active list of a pull-made frontier (it appends the chunk units)
                 ms_masks_to_list<T>(p, g, sm, f_cur, a_cur, u_cur, cur);
                 if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
                 list_valid = level;
+                const unsigned long long* const usrc[1] = {&cur->u_len};
+                unsigned long long uv[1];
+                cta_load_u64<1>(usrc, uv);
+                nunits = (long long)uv[0];
             }
-            long long nunits = (long long)__ldcg(&cur->u_len);
             if (gtid == 0) {
                 CountersMS* z = &ctl->slot[(level + 2) % 3];
                 z->a_len = 0;
@@ -787,7 +794,10 @@ __device__ void msbfs_body(const ParamsMS& p) {
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             long long nl = 0;
             if (dir == BFS_DIR_PULL) {
-                nl = (long long)__ldcg(&ctl->long_len);
+                const unsigned long long* const lsrc[1] = {&ctl->long_len};
+                unsigned long long lv[1];
+                cta_load_u64<1>(lsrc, lv);
+                nl = (long long)lv[0];
                 if (nl > 0) {
                     ms_long_rows<T>(p, g, sm, f_cur, live, nl);
                     if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -803,7 +813,10 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 for (long long v = gtid; v < g.n; v += gthreads) f_cur[v] = 0;
             }
             if (dir != BFS_DIR_PULL) {
-                long long an = (long long)__ldcg(&nxt->a_len);
+                const unsigned long long* const asrc[1] = {&nxt->a_len};
+                unsigned long long av[1];
+                cta_load_u64<1>(asrc, av);
+                long long an = (long long)av[0];
                 for (long long q = gtid; q < an; q += gthreads) {
                     int v = L.a_next[q];
                     p.seen[v] |= ((const unsigned long long*)L.f_next)[v];
