@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--sources", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip batched / learned / ER extras")
+    ap.add_argument("--profile-batched", type=int, default=0, metavar="R",
+                    help="only run R 64-lane batched launches of the workload's sources and exit (for ncu)")
     ap.add_argument("--policy-weights", default=os.path.join(ROOT, "paper_2607_17106_gb300", "policy_weights.npy"))
     return ap.parse_args()
 
@@ -351,6 +353,13 @@ def main():
     depth = torch.empty((k, n), dtype=torch.int32, device="cuda")
     parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
     opt = bg.options(batch=0)
+    if args.profile_batched > 0:
+        for _ in range(args.profile_batched):
+            g.run(sources, depth, parent, bg.options(batch=1))
+        g.sync()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batched": args.profile_batched, "workload": w.name, "sources": k}))
+        return 0
 
     def plain_step(events=None):
         for j in range(k):
@@ -440,8 +449,11 @@ def main():
             return bool(np.array_equal(depth.cpu().numpy(), depth_h))
 
         bms = time_batched(bg.options(batch=1))
+        # the same searches' minimum bytes (sum of B_min over the k sources)
+        # over the batched time: the roofline fraction of the batched form
         extra["batched_msbfs"] = {"gteps": edges / (bms * 1e-3) / 1e9, "ms_per_step": bms,
-                                  "speedup_vs_plain": ms_per_step / bms, "depth_equal_to_plain": same_depths()}
+                                  "speedup_vs_plain": ms_per_step / bms, "depth_equal_to_plain": same_depths(),
+                                  "roofline_frac": float(np.sum(bmin)) / (bms * 1e-3) / 1e9 / peak}
         try:
             from paper_2607_17106_gb300 import tune
             ot = tune.tuned_options(w.kind, n, info.m, batch=True)
@@ -466,7 +478,8 @@ def main():
                                        "depth_equal_to_plain": same_depths()}
             blms = time_batched(bg.options(batch=1, policy=bg.BFS_POLICY_MLP, mlp=pol))
             extra["batched_learned"] = {"gteps": edges / (blms * 1e-3) / 1e9, "ms_per_step": blms,
-                                        "speedup_vs_plain": ms_per_step / blms, "depth_equal_to_plain": same_depths()}
+                                        "speedup_vs_plain": ms_per_step / blms, "depth_equal_to_plain": same_depths(),
+                                        "roofline_frac": float(np.sum(bmin)) / (blms * 1e-3) / 1e9 / peak}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()
