@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(256) g_init(Params1 p, int32_t s, int32_t* dep
     }
     if (gtid == 0) {
         Ctl1* ctl = p.ctl;
-        int deg = __ldg(p.row_ptr + s + 1) - __ldg(p.row_ptr + s);
-        p.Q0[0] = s;
+        const int rb = __ldg(p.row_ptr + s), re = __ldg(p.row_ptr + s + 1);
+        const int deg = re - rb;
+        p.Q0[0] = make_int4(s, rb, re, 0);
         int nch = deg >= p.chunk ? (deg + p.chunk - 1) / p.chunk : 0;
         for (int c = 0; c < nch; ++c) p.U0[c] = make_int2(s, c);
         for (int k = 0; k < 3; ++k) {
@@ -185,10 +186,10 @@ __global__ void __launch_bounds__(256) g_q2bm_scatter(Params1 p) {
     const GHead h = cta_head(p.ctl);
     const int level = h.level;
     uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
-    const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
+    const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const long long f = h.f;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < f; q += (long long)gridDim.x * blockDim.x) {
-        int v = q_cur[q];
+        const int v = q_cur[q].x;
         atomicOr(f_cur + (v >> 5), 1u << (v & 31));
     }
 }
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(GT) g_bm2q(Params1 p) {
     __shared__ TileSmem<GT> sm;
     const int level = cta_head(p.ctl).level;
     uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
-    int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
+    int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
     int2* u_cur = (level & 1) ? p.U1 : p.U0;
     bitmap_to_queue<GT>(p, sm, f_cur, q_cur, u_cur, &p.ctl->slot[level % 3]);
 }
@@ -220,10 +221,12 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.next = nxt;
     L.ef = 0;
     L.cnt = 0;
-    L.qbuf = sm.qbuf + (threadIdx.x >> 5) * QBUF;
+    L.qv = sm.t.qv + (threadIdx.x >> 5) * QBUF;
+    L.qb = sm.t.qb + (threadIdx.x >> 5) * QBUF;
+    L.qe = sm.t.qe + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
     L.precheck = push_precheck(h.m_u, p.m);
-    const int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
+    const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const int2* u_cur = (level & 1) ? p.U1 : p.U0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     push_level<GT>(p, L, sm, DIR, q_cur, u_cur, f_cur, f, nunits, h.units_valid != 0);

@@ -73,7 +73,6 @@ extern __shared__ float bfs1_dyn_smem[];
 template <int T>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
-    __shared__ PullWarpSmem s_pull[T / 32];
     __shared__ float s_feat[BFS_MLP_IN];
     __shared__ float s_mlp_out;
     const float* mlp_w = nullptr;
@@ -101,8 +100,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (p.parent) p.parent[v] = (v == s) ? s : -1;
         }
         if (gtid == 0) {
-            int deg = __ldg(p.row_ptr + s + 1) - __ldg(p.row_ptr + s);
-            p.Q0[0] = s;
+            const int rb = __ldg(p.row_ptr + s), re = __ldg(p.row_ptr + s + 1);
+            const int deg = re - rb;
+            p.Q0[0] = make_int4(s, rb, re, 0);
             int nch = deg >= p.chunk ? (deg + p.chunk - 1) / p.chunk : 0;
             for (int c = 0; c < nch; ++c) p.U0[c] = make_int2(s, c);
             ctl->slot[0].q_len = 1;
@@ -132,6 +132,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
         Counters* nxt = &ctl->slot[(level + 1) % 3];
+        int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
         const unsigned long long* const csrc[3] = {&cur->q_len, &cur->u_len, &cur->e_f};
         unsigned long long cv[3];
         cta_load_u64<3>(csrc, cv);
@@ -159,7 +160,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             r.t_ns = (int64_t)globaltimer_ns();
             p.log[level] = r;
         }
-        int32_t* q_cur = (level & 1) ? p.Q1 : p.Q0;
         int2* u_cur = (level & 1) ? p.U1 : p.U0;
         uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
         uint32_t* f_nxt = (level & 1) ? p.F0 : p.F1;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             for (long long w = gtid; w < p.W; w += gthreads) f_cur[w] = 0;
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             for (long long q = gtid; q < f; q += gthreads) {
-                int v = __ldcg(q_cur + q);
+                const int v = __ldcg(q_cur + q).x;
                 atomicOr(f_cur + (v >> 5), 1u << (v & 31));
             }
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -200,11 +200,13 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.next = nxt;
         L.ef = 0;
         L.cnt = 0;
-        L.qbuf = sm.qbuf + warp * QBUF;
+        L.qv = sm.t.qv + warp * QBUF;
+        L.qb = sm.t.qb + warp * QBUF;
+        L.qe = sm.t.qe + warp * QBUF;
         L.qn = 0;
         L.precheck = push_precheck(m_u, p.m);
         if (dir == BFS_DIR_PULL) {
-            pull_level<false>(p, L, f_cur, f_nxt, s_pull[warp]);
+            pull_level<false>(p, L, f_cur, f_nxt, sm.pull[warp]);
         } else {
             push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
         }
@@ -320,7 +322,7 @@ static bfs_status ensure_ws1(bfs_graph* g, int32_t chunk, cudaStream_t st, Works
     w->ucap = (int64_t)units + 1;
     ok = ok && cudaMalloc(&w->P, w->W * 4) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i) {
-        ok = cudaMalloc(&w->F[i], w->W * 4) == cudaSuccess && cudaMalloc(&w->Q[i], (int64_t)g->n * 4) == cudaSuccess &&
+        ok = cudaMalloc(&w->F[i], w->W * 4) == cudaSuccess && cudaMalloc(&w->Q[i], (int64_t)g->n * sizeof(int4)) == cudaSuccess &&
              cudaMalloc(&w->U[i], w->ucap * sizeof(int2)) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&w->ctl, sizeof(Ctl1)) == cudaSuccess;

@@ -43,7 +43,7 @@ struct Workspace1 {
     int64_t ucap = 0;
     uint32_t* P = nullptr;
     uint32_t* F[2] = {nullptr, nullptr};
-    int32_t* Q[2] = {nullptr, nullptr};
+    int4* Q[2] = {nullptr, nullptr};
     int2* U[2] = {nullptr, nullptr};
     Ctl1* ctl = nullptr;
     int* d_sticky = nullptr;
@@ -75,8 +75,8 @@ struct Params1 {
     uint32_t* P;
     uint32_t* F0;
     uint32_t* F1;
-    int32_t* Q0;
-    int32_t* Q1;
+    int4* Q0;  // frontier queues: {vertex, row begin, row end, 0}
+    int4* Q1;
     int2* U0;
     int2* U1;
     int64_t ucap;
@@ -174,12 +174,14 @@ struct LevelCtx {
     int32_t level;          // i: discovered vertices get depth i+1
     int32_t* depth;         // outputs of this run
     int32_t* parent;
-    int32_t* q_next;
+    int4* q_next;
     int2* u_next;
     Counters* next;         // counters of F_{i+1}
     unsigned long long ef;  // this thread's share of e_f(F_{i+1})
     unsigned long long cnt; // this thread's share of |F_{i+1}| (pull levels)
-    int32_t* qbuf;          // this warp's staging buffer (QBUF entries)
+    int32_t* qv;            // this warp's staging of next-queue entries (QBUF
+    int32_t* qb;            // each): vertex, row begin, row end
+    int32_t* qe;
     int qn;                 // entries staged (warp-uniform)
     bool precheck;          // push: read P before the OR (most targets already visited)
 };
@@ -189,7 +191,9 @@ struct LevelCtx {
 __device__ __forceinline__ bool push_precheck(long long m_u, long long m) { return 2 * m_u < m; }
 
 // Move the warp's staged queue entries to the next queue: one atomic per
-// flush instead of one per claiming round.  Warp-uniform.
+// flush instead of one per claiming round.  An entry carries its vertex's row
+// bounds (loaded when the vertex was claimed), so expanding it next level
+// needs no row-offset load.  Warp-uniform.
 __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
     if (L.qn == 0) return;
     unsigned lane = lane_id();
@@ -197,7 +201,7 @@ __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
     if (lane == 0) base = atomicAdd(&L.next->q_len, (unsigned long long)L.qn);
     base = __shfl_sync(0xffffffffu, base, 0);
     __syncwarp();
-    for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = L.qbuf[i];
+    for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = make_int4(L.qv[i], L.qb[i], L.qe[i], 0);
     __syncwarp();
     L.qn = 0;
 }
@@ -238,14 +242,19 @@ __device__ __forceinline__ void emit_units_warp(const Params1& p, int2* u_out, C
 }
 
 // Record vertices claimed in a push level: depth/parent, staged next-queue
-// slot, degree sum, chunk units for big rows.  Warp-uniform call.
-__device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int deg) {
+// slot (with the row bounds rb..re of v), degree sum, chunk units for big
+// rows.  Warp-uniform call.
+__device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int rb, int re) {
     unsigned cm = __ballot_sync(0xffffffffu, claimed);
     if (!cm) return;
     int c = __popc(cm);
     if (L.qn + c > QBUF) flush_qbuf(L);
+    const int deg = re - rb;
     if (claimed) {
-        L.qbuf[L.qn + __popc(cm & lanemask_lt())] = v;
+        const int slot = L.qn + __popc(cm & lanemask_lt());
+        L.qv[slot] = v;
+        L.qb[slot] = rb;
+        L.qe[slot] = re;
         L.depth[v] = L.level + 1;
         if (L.parent) L.parent[v] = u;
         L.ef += (unsigned long long)deg;
@@ -288,33 +297,47 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
     } else if (want) {
         claimed = !(atomicOr(p.P + w, bit) & bit);
     }
-    emit(p, L, claimed, v, u, claimed ? re - rb : 0);
+    emit(p, L, claimed, v, u, rb, re);
 }
 
 // ------------------------------------------------------------ push tiles
+struct PullWarpSmem {
+    unsigned nb[32];                   // new bits of the block's words
+    int lv[32], lj[32], le[32], lb[32];  // deferred rows: vertex, next entry, end, row start
+    int nl;
+};
+
+// Shared memory of a CTA running level kernels.  Push levels use the tile
+// scratch and the warps' next-queue staging; pull levels use the per-warp
+// pull scratch; no level uses both, so they share storage.
 template <int T>
 struct TileSmem {
-    int off[T + 1];
-    int beg[T];
-    int lim[T];
-    int src[T];
+    union {
+        struct {
+            int off[T + 1];
+            int beg[T];
+            int lim[T];
+            int src[T];
+            int32_t qv[(T / 32) * QBUF];
+            int32_t qb[(T / 32) * QBUF];
+            int32_t qe[(T / 32) * QBUF];
+        } t;
+        PullWarpSmem pull[T / 32];
+    };
     int scan_tmp[33];
-    int32_t qbuf[(T / 32) * QBUF];
     unsigned long long red[T / 32];
     unsigned long long base;
 };
 
-// One CTA expands up to T frontier vertices (one per thread, u < 0 = none).
-// Rows of degree >= chunk are skipped when chunk units cover them.
+// One CTA expands up to T frontier vertices (one per thread, u < 0 = none)
+// whose rows are beg..end.  Rows of degree >= chunk are skipped when chunk
+// units cover them.
 template <int T>
-__device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int u, bool skip_big) {
+__device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int u, int beg, int end,
+                                          bool skip_big) {
     unsigned lane = lane_id();
-    int beg = 0, end = 0;
-    if (u >= 0) {
-        beg = __ldg(p.row_ptr + u);
-        end = __ldg(p.row_ptr + u + 1);
-        if (skip_big && end - beg >= p.chunk) end = beg;
-    }
+    if (u < 0) beg = end = 0;
+    if (skip_big && end - beg >= p.chunk) end = beg;
     // medium rows: cut into 32-edge segments that the CTA's warps take in
     // turn (a warp walking only its own lanes' rows would serialise them while
     // the other warps idle)
@@ -322,22 +345,22 @@ __device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSme
     int nseg_total;
     const int soff = block_exclusive_scan(med ? (end - beg + 31) >> 5 : 0, sm.scan_tmp, &nseg_total);
     if (nseg_total > 0) {
-        sm.off[threadIdx.x] = soff;
-        sm.beg[threadIdx.x] = beg;
-        sm.lim[threadIdx.x] = end;
-        sm.src[threadIdx.x] = u;
+        sm.t.off[threadIdx.x] = soff;
+        sm.t.beg[threadIdx.x] = beg;
+        sm.t.lim[threadIdx.x] = end;
+        sm.t.src[threadIdx.x] = u;
         __syncthreads();
         for (int s = (int)(threadIdx.x >> 5); s < nseg_total; s += T / 32) {
             // the row holding segment s: largest t with off[t] <= s
             int lo = 0, hi = T - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (sm.off[mid] <= s) lo = mid; else hi = mid - 1;
+                if (sm.t.off[mid] <= s) lo = mid; else hi = mid - 1;
             }
-            const int j = sm.beg[lo] + ((s - sm.off[lo]) << 5) + (int)lane;
-            const bool has = j < sm.lim[lo];
+            const int j = sm.t.beg[lo] + ((s - sm.t.off[lo]) << 5) + (int)lane;
+            const bool has = j < sm.t.lim[lo];
             const int v = has ? __ldg(p.col + j) : 0;
-            push_candidate(p, L, has, v, sm.src[lo]);
+            push_candidate(p, L, has, v, sm.t.src[lo]);
         }
         // the scan below passes a barrier before anything overwrites off/beg/src
     }
@@ -345,10 +368,10 @@ __device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSme
     // small rows: flatten (u, j) pairs over the CTA
     int deg = end - beg, total;
     int off = block_exclusive_scan(deg, sm.scan_tmp, &total);
-    sm.off[threadIdx.x] = off;
-    sm.beg[threadIdx.x] = beg;
-    sm.src[threadIdx.x] = u;
-    if (threadIdx.x == T - 1) sm.off[T] = total;
+    sm.t.off[threadIdx.x] = off;
+    sm.t.beg[threadIdx.x] = beg;
+    sm.t.src[threadIdx.x] = u;
+    if (threadIdx.x == T - 1) sm.t.off[T] = total;
     __syncthreads();
     for (int k0 = 0; k0 < total; k0 += T) {
         int k = k0 + threadIdx.x;
@@ -359,10 +382,10 @@ __device__ __forceinline__ void push_tile(const Params1& p, LevelCtx& L, TileSme
             int lo = 0, hi = T - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (sm.off[mid] <= k) lo = mid; else hi = mid - 1;
+                if (sm.t.off[mid] <= k) lo = mid; else hi = mid - 1;
             }
-            su = sm.src[lo];
-            v = __ldg(p.col + sm.beg[lo] + (k - sm.off[lo]));
+            su = sm.t.src[lo];
+            v = __ldg(p.col + sm.t.beg[lo] + (k - sm.t.off[lo]));
         }
         push_candidate(p, L, has, v, su);
     }
@@ -383,40 +406,40 @@ __device__ __forceinline__ void push_unit(const Params1& p, LevelCtx& L, int2 un
     }
 }
 
-// Push level: items are [chunk units of F_i] then [tiles of the frontier],
-// dealt to CTAs round-robin (units are equal-sized; tiles hold rows below
-// the chunk size).  Queue tiles hold about f / gridDim vertices (at most T),
-// so that a small frontier is spread over every CTA instead of a few full
-// tiles.
+// Push level.  Queue levels deal the frontier in passes of gridDim * T
+// entries: thread t of CTA b takes entry pass * gridDim * T + b + gridDim * t,
+// so a small frontier spreads over one thread of many CTAs.  Each entry carries
+// its row bounds.  Bitmap levels deal tiles of T/32 words of F_i round-robin.
+// Then the chunk units of F_i's big rows, round robin (their rows are skipped
+// in the tiles).
 template <int T>
-__device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int32_t* q_cur,
+__device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int4* q_cur,
                            const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, bool units_valid) {
-    long long per_tile = (f + gridDim.x - 1) / gridDim.x;
-    per_tile = per_tile < 1 ? 1 : (per_tile > T ? T : per_tile);
-    long long ntiles;
-    if (dir == BFS_DIR_PUSH_QUEUE) ntiles = (f + per_tile - 1) / per_tile;
-    else ntiles = (p.W + (T / 32) - 1) / (T / 32);
-    if (!units_valid) nunits = 0;
-    long long nitems = nunits + ntiles;
-    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
-        if (it < nunits) {
-            push_unit<T>(p, L, __ldcg(u_cur + it));
-        } else {
-            long long t = it - nunits;
-            int u = -1;
-            if (dir == BFS_DIR_PUSH_QUEUE) {
-                long long q = t * per_tile + threadIdx.x;
-                if (threadIdx.x < per_tile && q < f) u = __ldcg(q_cur + q);
-            } else {
-                long long w = t * (T / 32) + (threadIdx.x >> 5);
-                if (w < p.W) {
-                    unsigned fw = f_cur[w];
-                    if ((fw >> (threadIdx.x & 31)) & 1u) u = (int)(w * 32 + (threadIdx.x & 31));
+    const long long G = gridDim.x;
+    if (dir == BFS_DIR_PUSH_QUEUE) {
+        for (long long base = 0; base + blockIdx.x < f; base += G * T) {  // CTA-uniform
+            const long long q = base + blockIdx.x + G * threadIdx.x;
+            const int4 e = q < f ? __ldcg(q_cur + q) : make_int4(-1, 0, 0, 0);
+            push_tile<T>(p, L, sm, e.x, e.y, e.z, units_valid);
+        }
+    } else {
+        const long long ntiles = (p.W + (T / 32) - 1) / (T / 32);
+        for (long long t = blockIdx.x; t < ntiles; t += G) {
+            const long long w = t * (T / 32) + (threadIdx.x >> 5);
+            int u = -1, rb = 0, re = 0;
+            if (w < p.W) {
+                const unsigned fw = f_cur[w];
+                if ((fw >> (threadIdx.x & 31)) & 1u) {
+                    u = (int)(w * 32 + (threadIdx.x & 31));
+                    rb = __ldg(p.row_ptr + u);
+                    re = __ldg(p.row_ptr + u + 1);
                 }
             }
-            push_tile<T>(p, L, sm, u, units_valid);
+            push_tile<T>(p, L, sm, u, rb, re, units_valid);
         }
     }
+    if (units_valid)
+        for (long long it = blockIdx.x; it < nunits; it += G) push_unit<T>(p, L, __ldcg(u_cur + it));
     flush_qbuf(L);
 }
 
@@ -565,11 +588,7 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
 // scanned by the whole warp 32 entries at a time.  New bits of the block's
 // words collect in shared memory; the warp then writes its words of F_{i+1}
 // and P with plain stores (it owns them).
-struct PullWarpSmem {
-    unsigned nb[32];                   // new bits of the block's words
-    int lv[32], lj[32], le[32], lb[32];  // deferred rows: vertex, next entry, end, row start
-    int nl;
-};
+
 
 // Position of the r-th (0-based) set bit of m; m must have more than r bits set.
 __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
@@ -790,7 +809,7 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
 // F_i bitmap -> queue Q_i (ascending vertex order inside each CTA chunk) and
 // chunk units for its big rows.  Cursor: cur->conv.
 template <int T>
-__device__ void bitmap_to_queue(const Params1& p, TileSmem<T>& sm, const uint32_t* f_cur, int32_t* q_cur, int2* u_cur,
+__device__ void bitmap_to_queue(const Params1& p, TileSmem<T>& sm, const uint32_t* f_cur, int4* q_cur, int2* u_cur,
                                 Counters* cur) {
     for (long long wb = (long long)blockIdx.x * T; wb < p.W; wb += (long long)gridDim.x * T) {
         long long w = wb + threadIdx.x;
@@ -804,10 +823,10 @@ __device__ void bitmap_to_queue(const Params1& p, TileSmem<T>& sm, const uint32_
         while (fw) {
             int b = __ffs(fw) - 1;
             fw &= fw - 1;
-            int v = (int)(w * 32 + b);
-            q_cur[base + off + r++] = v;
-            int deg = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
-            if (deg >= p.chunk) emit_units(p, u_cur, cur, v, deg);
+            const int v = (int)(w * 32 + b);
+            const int rb = __ldg(p.row_ptr + v), re = __ldg(p.row_ptr + v + 1);
+            q_cur[base + off + r++] = make_int4(v, rb, re, 0);
+            if (re - rb >= p.chunk) emit_units(p, u_cur, cur, v, re - rb);
         }
         __syncthreads();
     }
