@@ -438,8 +438,32 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
             push_tile<T>(p, L, sm, u, rb, re, units_valid);
         }
     }
-    if (units_valid)
+    if (!units_valid || nunits == 0) {
+        flush_qbuf(L);
+        return;
+    }
+    if (p.chunk <= T && T % p.chunk == 0 && p.chunk % 32 == 0) {
+        // T / chunk units at a time, one per group of chunk threads (whole
+        // warps), one edge per thread: a CTA is not left three-quarters idle
+        // on 256-edge units
+        const int per = T / p.chunk;
+        const int grp = (int)threadIdx.x / p.chunk, lt = (int)threadIdx.x % p.chunk;
+        for (long long it = (long long)blockIdx.x * per; it < nunits; it += G * per) {  // CTA-uniform
+            const long long ui = it + grp;
+            int u = 0, j = 0, hi = 0;
+            if (ui < nunits) {
+                const int2 un = __ldcg(u_cur + ui);
+                u = un.x;
+                const int b = __ldg(p.row_ptr + u), e = __ldg(p.row_ptr + u + 1);
+                j = b + un.y * p.chunk + lt;
+                hi = min(e, b + (un.y + 1) * p.chunk);
+            }
+            const bool has = j < hi;
+            push_candidate(p, L, has, has ? __ldg(p.col + j) : 0, u);
+        }
+    } else {
         for (long long it = blockIdx.x; it < nunits; it += G) push_unit<T>(p, L, __ldcg(u_cur + it));
+    }
     flush_qbuf(L);
 }
 
