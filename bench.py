@@ -509,7 +509,7 @@ def main():
             "config": {"workload": f"{w.name}: {describe(w)}, symmetrised+dedup, n={n}, m={info.m} directed; "
                                    f"{k} seeded sources one at a time", "sources_per_step": k, "edges_per_step": edges,
                        "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
-                       "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=14 beta=24"},
+                       "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=8 beta=48"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": k * args.steps,
             "clocks": clk, **extra,
         }

@@ -128,12 +128,12 @@ typedef struct {
     uint32_t struct_size;    /* sizeof(bfs_options); set by bfs_options_init */
     int32_t mode;            /* BFS_MODE_* */
     int32_t policy;          /* BFS_POLICY_* */
-    float alpha;             /* Beamer alpha (14) */
-    float beta;              /* Beamer beta (24) */
+    float alpha;             /* Beamer alpha (8) */
+    float beta;              /* Beamer beta (48) */
     float gamma;             /* push levels read the bitmap when f > n / gamma (16) */
-    int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (256) */
+    int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (1024) */
     int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
-    int32_t pull_serial;     /* pull: entries of one row tested per flattened warp round (32; MS-BFS: twice this many entries are scanned per thread before a warp takes over) */
+    int32_t pull_serial;     /* pull: row entries a lane tests before its row is finished by the whole warp (16; MS-BFS: twice this many) */
     int32_t block_threads;   /* threads per CTA of the persistent single-source kernel: 256, 512 or 1024 (1024) */
     int32_t blocks_per_sm;   /* CTAs per SM, 0 = as many as fit (persistent/cooperative launch) */
     int32_t claim_aggregate; /* push: warp-aggregate the visited-bitmap OR by word (0) */

@@ -82,12 +82,12 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->struct_size = sizeof(bfs_options);
     o->mode = BFS_MODE_PERSISTENT;
     o->policy = BFS_POLICY_HEURISTIC;
-    o->alpha = 14.0f;
-    o->beta = 24.0f;
+    o->alpha = 8.0f;
+    o->beta = 48.0f;
     o->gamma = 16.0f;
-    o->chunk = 256;
+    o->chunk = 1024;
     o->medium = 32;
-    o->pull_serial = 32;
+    o->pull_serial = 16;
     o->block_threads = 1024;
     o->blocks_per_sm = 0;
     o->claim_aggregate = 0;

@@ -32,7 +32,7 @@ SINGLE_SPACE = {
     "block_threads": [256, 512, 1024],
     "chunk": [128, 256, 1024],
     "medium": [16, 32, 64],
-    "pull_serial": [8, 32],
+    "pull_serial": [8, 16, 32],
     "claim_aggregate": [0, 1],
     "alpha": [8.0, 14.0, 24.0],
     "beta": [12.0, 24.0, 48.0],
@@ -43,8 +43,8 @@ BATCH_SPACE = {
     "chunk": [128, 256, 1024],
     "medium": [16, 32],
     "pull_serial": [16, 32, 64],
-    "alpha": [4.0, 14.0, 64.0],
-    "beta": [24.0],
+    "alpha": [4.0, 8.0, 14.0, 64.0],
+    "beta": [24.0, 48.0],
 }
 
 

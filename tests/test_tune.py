@@ -15,7 +15,7 @@ def _lib():
 
 
 def test_coordinate_search_finds_the_separable_minimum(monkeypatch):
-    best = {"chunk": 1024, "medium": 16, "alpha": 24.0}
+    best = {"chunk": 256, "medium": 16, "alpha": 24.0}  # every knob off its library default
 
     def fake_time(g, sources, opt, batch, reps=3):
         t = 100.0
