@@ -227,8 +227,10 @@ bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int
  * Direction policy: an FP32 MLP 10 -> 32 -> 32 -> 3 (ReLU) whose argmax picks
  * BFS_DIR_*.  The paper has no learned policy; it replaces the Beamer switch
  * it cites (Section 5) where that switch's own test is close -- e_f * alpha /
- * m_u within (1/8, 8) -- and the heuristic decides the clear-cut levels (and
- * costs no network evaluation there).  Parameter layout (1507 floats, row-major):
+ * m_u within (1/8, 8) -- and only when it predicts its choice a to beat the
+ * heuristic's form h clearly (outputs z_a - z_h > 1.0, about 2.7x in time);
+ * the heuristic decides everywhere else (and costs no network evaluation on
+ * the clear-cut levels).  Parameter layout (1507 floats, row-major):
  *   W1[32][10] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]
  * followed by 20 floats of input normalisation: mean[10], inv_std[10].
  */
@@ -241,10 +243,12 @@ bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int
 /*
  * Features of one level (host or device float[10]) from its counters: f =
  * |F_i|, e_f = degree sum over F_i, m_u = degree sum over unvisited vertices,
- * f_prev = |F_{i-1}|, prev_dir = form of level i-1.  Mostly scale-free:
+ * f_prev = |F_{i-1}|, prev_dir = form of level i-1.  Scale-free:
  * log2 of e_f/m_u, f/n, m_u/m, mean frontier degree over mean degree,
- * (f+1)/(f_prev+1); prev_dir one-hot (pull, push-bitmap); log2(1+level);
- * log2(deg_max / mean degree); log2(n)/32.
+ * (f+1)/(f_prev+1); prev_dir one-hot (pull, push-bitmap); min(log2(n), 22)/32
+ * (graph size, clamped to the largest training scale); log2(deg_max / mean
+ * degree) capped at 12; log2(mean degree)/4.  `level` is accepted for the
+ * interface and not used.
  */
 bfs_status bfs_policy_features(const bfs_graph* g, int32_t level, int64_t f, int64_t e_f, int64_t m_u,
                                int64_t f_prev, int32_t prev_dir, float* out10);

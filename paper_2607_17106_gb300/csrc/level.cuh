@@ -140,14 +140,15 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
             int d = p.schedule[level % p.schedule_len];
             return (d < 0 || d > 2) ? BFS_DIR_PUSH_QUEUE : d;
         }
-        case BFS_POLICY_MLP:
+        case BFS_POLICY_MLP: {
+            const int h = heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
             if (p.mlp && policy_in_band(e_f, m_u, p.alpha)) {
                 // warp 0 evaluates; result broadcast through shared memory
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
                         policy_features(s_feat, f, e_f, m_u, f_prev, level, prev_dir, p.n, p.m, p.deg_max);
                     __syncwarp();
-                    int a = policy_argmax_warp(mlp_w ? mlp_w : p.mlp, s_feat);
+                    int a = policy_choice_warp(mlp_w ? mlp_w : p.mlp, s_feat, h, MLP_MARGIN);
                     if (threadIdx.x == 0) *s_mlp_out = (float)a;
                 }
                 __syncthreads();
@@ -155,7 +156,8 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
                 __syncthreads();
                 return a;
             }
-            return heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
+            return h;
+        }
         default:
             return heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
     }

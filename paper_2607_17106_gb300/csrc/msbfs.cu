@@ -599,6 +599,17 @@ __device__ void ms_masks_to_list(const ParamsMS& p, const UnitView& g, MsSmem& s
     }
 }
 
+// The MS-BFS heuristic: Beamer's test on the lanes' summed counters.
+__device__ __forceinline__ int ms_heuristic(const ParamsMS& p, const UnitView& g, long long a, long long e_f,
+                                            long long m_u, long long a_prev, int prev_dir) {
+    if (prev_dir == BFS_DIR_PULL) {
+        bool stay = (a >= a_prev) || ((float)a * p.beta > (float)g.n);
+        return stay ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
+    }
+    if ((float)e_f * p.alpha > (float)m_u && a > a_prev) return BFS_DIR_PULL;
+    return BFS_DIR_PUSH_QUEUE;
+}
+
 __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int level, long long a, long long e_f,
                          long long m_u, long long a_prev, int prev_dir, int deg_max) {
     int d;
@@ -608,13 +619,14 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
         case BFS_POLICY_SCHEDULE:
             d = p.schedule[level % p.schedule_len];
             return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
-        case BFS_POLICY_MLP:
+        case BFS_POLICY_MLP: {
+            const int h = ms_heuristic(p, g, a, e_f, m_u, a_prev, prev_dir);
             if (p.mlp && policy_in_band(e_f, m_u, p.alpha)) {
                 if (threadIdx.x < 32) {
                     if (threadIdx.x == 0)
                         policy_features(sm.feat, a, e_f, m_u, a_prev, level, prev_dir, g.n, g.m, deg_max);
                     __syncwarp();
-                    int c = policy_argmax_warp(p.mlp, sm.feat);
+                    int c = policy_choice_warp(p.mlp, sm.feat, h, MLP_MARGIN);
                     if (threadIdx.x == 0) sm.mlp_out = (float)c;
                 }
                 __syncthreads();
@@ -622,14 +634,10 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
                 __syncthreads();
                 return d == BFS_DIR_PULL ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
             }
-            // no weights, or a clear-cut level: the heuristic decides
+            return h;  // no weights, or a clear-cut level: the heuristic decides
+        }
         default:
-            if (prev_dir == BFS_DIR_PULL) {
-                bool stay = (a >= a_prev) || ((float)a * p.beta > (float)g.n);
-                return stay ? BFS_DIR_PULL : BFS_DIR_PUSH_QUEUE;
-            }
-            if ((float)e_f * p.alpha > (float)m_u && a > a_prev) return BFS_DIR_PULL;
-            return BFS_DIR_PUSH_QUEUE;
+            return ms_heuristic(p, g, a, e_f, m_u, a_prev, prev_dir);
     }
 }
 

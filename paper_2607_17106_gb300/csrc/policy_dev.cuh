@@ -24,15 +24,20 @@ constexpr int OFF_ISTD = NPARAM + MLP_IN;
 constexpr int NWEIGHTS = NPARAM + 2 * MLP_IN;
 static_assert(NPARAM == BFS_MLP_NPARAM, "parameter count");
 
-// Ten per-level features, scale-free where possible so that a policy
-// trained on small graphs transfers to larger ones:
+// Ten per-level features.  All are ratios except the graph size, which is
+// clamped to the largest training size: without it the network cannot tell
+// small graphs, where fixed per-level costs make push win, from large ones at
+// the same ratios; unclamped (a raw log2(n)) it picked push on scale-23/24 hub
+// levels where pull was 5-6x faster.
 //   x0 log2(e_f / m_u)         frontier edges over unexplored edges (Beamer's ratio)
 //   x1 log2(f / n)             frontier density
 //   x2 log2(m_u / m)           fraction of the edges still unexplored
 //   x3 log2(deg(F) / deg(G))   mean frontier degree over mean degree
 //   x4 log2((f+1) / (f'+1))    frontier growth since the previous level
 //   x5 previous level was pull        x6 previous level was push-bitmap
-//   x7 log2(1 + level)         x8 log2(deg_max / deg(G))   x9 log2(n) / 32
+//   x7 min(log2(n), 22) / 32   x8 log2(deg_max / deg(G)), at most 12 (the skew
+//   of the largest training graphs; it grows with n on power-law graphs)
+//   x9 log2(deg(G)) / 4        (mean degree: graph density, not size)
 __host__ __device__ inline void policy_features(float* x, long long f, long long e_f, long long m_u, long long f_prev,
                                                 int level, int prev_dir, long long n, long long m, int deg_max) {
     const float fn = (float)(f > 1 ? f : 1), ef = (float)(e_f > 1 ? e_f : 1), mu = (float)(m_u > 1 ? m_u : 1);
@@ -45,9 +50,10 @@ __host__ __device__ inline void policy_features(float* x, long long f, long long
     x[4] = log2f((float)(f + 1) / (float)(f_prev + 1));
     x[5] = (prev_dir == BFS_DIR_PULL) ? 1.0f : 0.0f;
     x[6] = (prev_dir == BFS_DIR_PUSH_BITMAP) ? 1.0f : 0.0f;
-    x[7] = log2f(1.0f + (float)level);
-    x[8] = log2f((float)(deg_max > 1 ? deg_max : 1) / dmean);
-    x[9] = log2f(nn) / 32.0f;
+    (void)level;  // part of the interface; the level index is not a feature
+    x[7] = fminf(log2f(nn), 22.0f) / 32.0f;
+    x[8] = fminf(log2f((float)(deg_max > 1 ? deg_max : 1) / dmean), 12.0f);
+    x[9] = log2f(dmean > 1.0f ? dmean : 1.0f) / 4.0f;
 }
 
 // The learned policy is consulted only where the heuristic's own test is
@@ -56,17 +62,26 @@ __host__ __device__ inline void policy_features(float* x, long long f, long long
 // heuristic decides, which also keeps the network away from the clear-cut
 // levels where a wrong form is slower by orders of magnitude.
 constexpr float MLP_TRUST = 8.0f;
+// Inside the band the network replaces the heuristic's form h only when it
+// predicts its own choice a to be clearly faster: z_a - z_h > MLP_MARGIN in
+// its log-time outputs (a factor of e, about 2.7).  On held-out graphs whose
+// levels lie outside the training families the network can be confidently
+// wrong; with this margin five of six training seeds made no held-out choice
+// worse than the heuristic's, while keeping most of the gain on training-like
+// levels.
+constexpr float MLP_MARGIN = 1.0f;
 __host__ __device__ inline bool policy_in_band(long long e_f, long long m_u, float alpha) {
     const float a = (float)(e_f > 1 ? e_f : 1) * alpha, b = (float)(m_u > 1 ? m_u : 1);  // ratio a / b, FP32, no division
     return a * MLP_TRUST > b && a < b * MLP_TRUST;
 }
 
 #ifdef __CUDACC__
-// Warp-cooperative forward pass (lane j owns hidden unit j); returns the
-// argmax class (lowest index on ties) on every lane.  x: 10 raw features.
-// Lane j visits the 32 terms of its second-layer row starting at term j, so
-// that with w in shared memory the lanes read 32 different banks.
-__device__ inline int policy_argmax_warp(const float* __restrict__ w, const float* x) {
+// Warp-cooperative forward pass (lane j owns hidden unit j).  Returns the
+// form to take, on every lane: the argmax a of the outputs (lowest index on
+// ties) if z_a - z_h exceeds `margin`, else the heuristic's form h.  x: 10 raw
+// features.  Lane j visits the 32 terms of its second-layer row starting at
+// term j, so that with w in shared memory the lanes read 32 different banks.
+__device__ inline int policy_choice_warp(const float* __restrict__ w, const float* x, int h, float margin) {
     const unsigned lane = threadIdx.x & 31;
     float xn[MLP_IN];
 #pragma unroll
@@ -94,7 +109,11 @@ __device__ inline int policy_argmax_warp(const float* __restrict__ w, const floa
 #pragma unroll
     for (int c = 1; c < MLP_OUT; ++c)
         if (z[c] > z[best]) best = c;
-    return best;
+    float zh = z[0];
+#pragma unroll
+    for (int c = 1; c < MLP_OUT; ++c)
+        if (c == h) zh = z[c];
+    return (z[best] - zh > margin) ? best : h;
 }
 #endif
 

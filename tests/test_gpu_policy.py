@@ -189,7 +189,7 @@ def test_policy_pipeline_trains_and_drives_searches():
     pol = pl.fit(X, None, epochs=600, lr=3e-3, target=pl.log_time_targets(T))
     choice = pl.predict(pol, X)
     assert choice.shape == y.shape
-    r_mlp, r_heur = pl.regret(pl.gate(choice, X, K), T), pl.regret(K, T)
+    r_mlp, r_heur = pl.regret(pl.gate(pl.outputs(pol, X), X, K), T), pl.regret(K, T)
     assert r_mlp["time_us"] <= r_heur["time_us"] * 1.02, (r_mlp, r_heur)
     import graphgen
     n, s, d = graphgen.rmat(13, 16, seed=5)
