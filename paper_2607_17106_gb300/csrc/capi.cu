@@ -146,23 +146,48 @@ extern "C" bfs_status bfs_run(const bfs_graph* gc, const int32_t* sources, int32
         }
         return BFS_OK;
     }
-    // host outputs: stage through device buffers
-    int32_t *dd = nullptr, *dp = nullptr;
-    if (cudaMallocAsync(&dd, n * 4, st) != cudaSuccess || (parent && cudaMallocAsync(&dp, n * 4, st) != cudaSuccess)) {
+    // host outputs: two pairs of device staging buffers; the search of source
+    // j+1 (on `st`) overlaps the copy of source j's outputs (on a copy stream),
+    // and the host waits once, at the end
+    int32_t *dd[2] = {nullptr, nullptr}, *dp[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t searched[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaMallocAsync(&dd[b], n * 4, st) == cudaSuccess &&
+             (!parent || cudaMallocAsync(&dp[b], n * 4, st) == cudaSuccess) &&
+             cudaEventCreateWithFlags(&searched[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
-        if (dd) cudaFreeAsync(dd, st);
-        return fail(BFS_ENOMEM, "staging buffers");
+        s = fail(BFS_ENOMEM, "staging buffers");
     }
     for (int j = 0; j < k && s == BFS_OK; ++j) {
-        s = run_single(g, src[j], dd, dp, o, mlp, st);
-        if (s != BFS_OK) break;
-        cudaError_t e = cudaMemcpyAsync(depth + j * n, dd, n * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent + j * n, dp, n * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        const int b = j & 1;
+        cudaError_t e = cudaSuccess;
+        if (j >= 2) e = cudaStreamWaitEvent(st, copied[b], 0);  // buffer b's previous copy is done
+        if (e == cudaSuccess) {
+            s = run_single(g, src[j], dd[b], dp[b], o, mlp, st);
+            if (s != BFS_OK) break;
+            e = cudaEventRecord(searched[b], st);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, searched[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(depth + j * n, dd[b], n * 4, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent + j * n, dp[b], n * 4, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
         if (e != cudaSuccess) s = cuda_fail(e, "copy outputs to host");
     }
-    cudaFreeAsync(dd, st);
-    if (dp) cudaFreeAsync(dp, st);
+    if (cs) {
+        cudaError_t e = cudaStreamSynchronize(cs);  // every copy has landed in host memory
+        if (e != cudaSuccess && s == BFS_OK) s = cuda_fail(e, "copy outputs to host");
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (dd[b]) cudaFreeAsync(dd[b], st);
+        if (dp[b]) cudaFreeAsync(dp[b], st);
+        if (searched[b]) cudaEventDestroy(searched[b]);
+        if (copied[b]) cudaEventDestroy(copied[b]);
+    }
+    if (cs) cudaStreamDestroy(cs);
     if (s == BFS_OK) s = sync_graph(g, st);
     return s;
 }
