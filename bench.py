@@ -410,6 +410,13 @@ def main():
     mean_launch_s = float(np.mean(launch_ms)) * 1e-3
     mean_bmin = float(np.mean(bmin))
     achieved = mean_bmin / mean_launch_s / 1e9
+    # Graph500-style per-search TEPS: each search's edges over its own launch time
+    per_src = np.array([teps_edges(stats[j]) / (ev[si][j][0].elapsed_time(ev[si][j][1]) * 1e-3) / 1e9
+                        for si in range(args.steps) for j in range(k)])
+    teps_stats = {"median_gteps": float(np.median(per_src)),
+                  "harmonic_mean_gteps": float(len(per_src) / np.sum(1.0 / np.maximum(per_src, 1e-12))),
+                  "min_gteps": float(per_src.min()), "max_gteps": float(per_src.max()),
+                  "searches": int(len(per_src))}
     roof = {"bound": "hbm", "kernel": "bfs1_kernel (persistent level loop)", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
             "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS, "bytes_per_launch": mean_bmin,
@@ -464,6 +471,15 @@ def main():
                                                                               "alpha", "beta")}}
         except Exception as exc:  # no cache entry for this device/graph class
             extra["batched_tuned"] = {"skipped": str(exc)[:120]}
+        # push advance / visited update arrangements (Variants 13/14 and 20/23
+        # against the fused claim), all 64 sources, heuristic directions
+        fms, _ = time_single(bg.options(batch=0))
+        pv = {"fused_ms_per_step": fms}
+        for name, pf in (("filter", bg.BFS_PUSH_FILTER), ("filter_predicated", bg.BFS_PUSH_FILTER_PREDICATED)):
+            vms, _ = time_single(bg.options(batch=0, push_filter=pf))
+            pv[name] = {"gteps": edges / (vms * 1e-3) / 1e9, "ms_per_step": vms, "speedup_vs_fused": fms / vms,
+                        "depth_equal_to_plain": same_depths()}
+        extra["push_variants"] = pv
         gms, cnt = time_single(bg.options(batch=0, mode=bg.BFS_MODE_GRAPH), 8)
         pms, _ = time_single(bg.options(batch=0), 8)
         extra["graph_mode_single"] = {"sources": cnt, "ms_graph_mode": gms, "ms_persistent": pms,
@@ -510,7 +526,8 @@ def main():
                                    f"{k} seeded sources one at a time", "sources_per_step": k, "edges_per_step": edges,
                        "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
                        "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=8 beta=48"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": k * args.steps,
+            "roofline": roof, "per_search": teps_stats, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": k * args.steps,
             "clocks": clk, **extra,
         }
         print(json.dumps(line))

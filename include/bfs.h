@@ -104,6 +104,18 @@ enum {
     BFS_MODE_GRAPH = 2       /* CUDA graph with a conditional WHILE node: no host work per level */
 };
 
+/* How a push level's advance and its visited update are arranged (Section 7.2:
+ * the conflict/predicate and visited-mask variants).  Single-source persistent
+ * and host-loop drives; MS-BFS batches always claim during the advance. */
+enum {
+    BFS_PUSH_FUSED = 0,             /* each neighbour is claimed in P during the advance (default) */
+    BFS_PUSH_FILTER = 1,            /* Variants 13/14: the advance appends every (neighbour, source) pair
+                                       to an edge frontier without a predicate; after a grid barrier a
+                                       filter pass claims them in P and records depth, parent and F_{i+1} */
+    BFS_PUSH_FILTER_PREDICATED = 2  /* Variants 20/23: the advance appends only neighbours not yet set in P;
+                                       the visited update happens in the filter pass */
+};
+
 /* Per-level direction policy. */
 enum {
     BFS_POLICY_HEURISTIC = 0, /* Beamer: push->pull if e_f > m_u/alpha, pull->push if f < n/beta */
@@ -146,6 +158,9 @@ typedef struct {
     int32_t level_log_cap;
     int32_t* levels_out;     /* optional host int32: number of levels executed (k = 1: last run) */
     int32_t batch;           /* k > 1: 1 = 64-lane MS-BFS batches (default), 0 = one source at a time */
+    int32_t push_filter;     /* BFS_PUSH_* (BFS_PUSH_FUSED).  A filter form holds an edge frontier of up to
+                                m (target, source) pairs, 8 B each, allocated on first use; the CUDA-graph
+                                drive rejects it with EINVAL */
 } bfs_options;
 
 /* Fill `opt` with the defaults listed above. */

@@ -52,6 +52,7 @@ void free_ws1(Workspace1* w) {
         cudaFree(w->Q[i]);
         cudaFree(w->U[i]);
     }
+    cudaFree(w->E);
     cudaFree(w->ctl);
     cudaFree(w->d_sticky);
     cudaFree(w->stage_depth);
@@ -190,6 +191,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             z->u_len = 0;
             z->e_f = 0;
             z->conv = 0;
+            z->e_len = 0;
         }
         LevelCtx L;
         L.level = level;
@@ -209,6 +211,14 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             pull_level<false>(p, L, f_cur, f_nxt, sm.pull[warp]);
         } else {
             push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
+            if (p.push_filter != BFS_PUSH_FUSED) {
+                // the advance is complete everywhere before any pair is claimed
+                if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+                const unsigned long long* const esrc[1] = {&nxt->e_len};
+                unsigned long long ev[1];
+                cta_load_u64<1>(esrc, ev);
+                filter_level<T>(p, L, (long long)min(ev[0], (unsigned long long)p.ecap));
+            }
         }
         // e_f (and |F_{i+1}| for pull) of the next frontier: one atomic per CTA
         unsigned long long ef = warp_sum(L.ef);
@@ -397,6 +407,22 @@ static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o,
     p.medium = o.medium;
     p.pull_serial = o.pull_serial;
     p.aggregate = o.claim_aggregate;
+    p.push_filter = o.push_filter;
+    if (o.push_filter != BFS_PUSH_FUSED) {
+        // edge frontier: one level's advance appends at most m pairs
+        if (w->ecap < g->m) {
+            cudaFree(w->E);
+            w->E = nullptr;
+            w->ecap = 0;
+            if (cudaMalloc(&w->E, (size_t)g->m * sizeof(int2)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(BFS_ENOMEM, "edge frontier of %lld pairs", (long long)g->m);
+            }
+            w->ecap = g->m;
+        }
+        p.E = w->E;
+        p.ecap = w->ecap;
+    }
     p.timeout_ns = o.barrier_timeout_ns;
     p.max_levels = o.max_levels > 0 ? o.max_levels : g->n + 1;
     if (o.policy == BFS_POLICY_SCHEDULE) {

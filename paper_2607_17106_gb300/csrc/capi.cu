@@ -91,6 +91,7 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->block_threads = 1024;
     o->blocks_per_sm = 0;
     o->claim_aggregate = 0;
+    o->push_filter = BFS_PUSH_FUSED;
     o->barrier_timeout_ns = 2000000000ll;
     o->batch = 1;
 }
@@ -109,6 +110,10 @@ static bfs_status check_options(const bfs_options* in, bfs_options* o) {
     if (o->barrier_timeout_ns <= 0) return fail(BFS_EINVAL, "barrier_timeout_ns must be > 0");
     if (o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
         return fail(BFS_EINVAL, "block_threads must be 256, 512 or 1024");
+    if (o->push_filter < BFS_PUSH_FUSED || o->push_filter > BFS_PUSH_FILTER_PREDICATED)
+        return fail(BFS_EINVAL, "bad push_filter %d", o->push_filter);
+    if (o->push_filter != BFS_PUSH_FUSED && o->mode == BFS_MODE_GRAPH)
+        return fail(BFS_EINVAL, "push_filter needs the persistent or host-loop drive");
     return BFS_OK;
 }
 

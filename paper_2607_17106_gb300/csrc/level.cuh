@@ -13,6 +13,7 @@ struct Counters {
     unsigned long long u_len;  // chunk units appended for the next level
     unsigned long long e_f;    // sum of out-degrees of the appended vertices
     unsigned long long conv;   // cursor of a bitmap -> queue conversion of this frontier
+    unsigned long long e_len;  // push_filter: (target, source) pairs in the edge frontier of the level
 };
 
 struct Ctl1 {
@@ -45,6 +46,8 @@ struct Workspace1 {
     uint32_t* F[2] = {nullptr, nullptr};
     int4* Q[2] = {nullptr, nullptr};
     int2* U[2] = {nullptr, nullptr};
+    int2* E = nullptr;  // push_filter: edge frontier, capacity ecap pairs (allocated on first use)
+    int64_t ecap = 0;
     Ctl1* ctl = nullptr;
     int* d_sticky = nullptr;
     int32_t* stage_depth = nullptr;
@@ -80,6 +83,8 @@ struct Params1 {
     int2* U0;
     int2* U1;
     int64_t ucap;
+    int2* E;       // push_filter: edge frontier of the level, {target, source}
+    int64_t ecap;
     Ctl1* ctl;
     int32_t src_value;
     int* sticky;          // first device error of any run, cleared by the host
@@ -95,6 +100,7 @@ struct Params1 {
     int32_t deg_max;
     // tuning
     int32_t chunk, medium, pull_serial, aggregate;
+    int32_t push_filter;  // BFS_PUSH_FUSED / _FILTER / _FILTER_PREDICATED
     int64_t timeout_ns;
     int32_t max_levels;
     bfs_level_record* log;
@@ -265,8 +271,9 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
     emit_units_warp(p, L.u_next, L.next, claimed && deg >= p.chunk, v, deg);
 }
 
-// Push candidate (u -> v): claim v in P if not yet visited.  Warp-uniform.
-__device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bool has, int v, int u) {
+// Claim v for parent u in P if not yet visited, and record the claim.
+// Warp-uniform.
+__device__ __forceinline__ void claim_candidate(const Params1& p, LevelCtx& L, bool has, int v, int u) {
     bool want = false;
     unsigned w = 0, bit = 0;
     if (has) {
@@ -300,6 +307,71 @@ __device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bo
         claimed = !(atomicOr(p.P + w, bit) & bit);
     }
     emit(p, L, claimed, v, u, rb, re);
+}
+
+// push_filter: move the warp's staged (target, source) pairs to the level's
+// edge frontier, one atomic per flush.  Warp-uniform.
+__device__ __forceinline__ void flush_pairs(const Params1& p, LevelCtx& L) {
+    if (L.qn == 0) return;
+    const unsigned lane = lane_id();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&L.next->e_len, (unsigned long long)L.qn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    if (base + (unsigned long long)L.qn <= (unsigned long long)p.ecap) {
+        for (int i = (int)lane; i < L.qn; i += 32) p.E[base + i] = make_int2(L.qv[i], L.qb[i]);
+    } else if (lane == 0) {
+        atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
+    }
+    __syncwarp();
+    L.qn = 0;
+}
+
+// End of a push level's expansion: staged queue entries, or staged pairs when
+// the claims are left to a filter pass.  Warp-uniform.
+__device__ __forceinline__ void flush_push(const Params1& p, LevelCtx& L) {
+    if (p.push_filter != BFS_PUSH_FUSED) flush_pairs(p, L);
+    else flush_qbuf(L);
+}
+
+// Push candidate (u -> v).  Fused (the default): claim v at once.  With a
+// filter pass, the advance only appends (v, u) to the level's edge frontier:
+// every pair (BFS_PUSH_FILTER, Variants 13/14: advance without the predicate),
+// or those whose v is not yet set in P (BFS_PUSH_FILTER_PREDICATED, Variants
+// 20/23: the visited test in the advance, the visited update in the filter).
+// The warp's queue staging holds the pairs (target in qv, source in qb).
+// Warp-uniform.
+__device__ __forceinline__ void push_candidate(const Params1& p, LevelCtx& L, bool has, int v, int u) {
+    if (p.push_filter == BFS_PUSH_FUSED) {
+        claim_candidate(p, L, has, v, u);
+        return;
+    }
+    bool want = has;
+    if (has && p.push_filter == BFS_PUSH_FILTER_PREDICATED) want = !(p.P[(unsigned)v >> 5] & (1u << (v & 31)));
+    const unsigned cm = __ballot_sync(0xffffffffu, want);
+    if (!cm) return;
+    const int c = __popc(cm);
+    if (L.qn + c > QBUF) flush_pairs(p, L);
+    if (want) {
+        const int slot = L.qn + __popc(cm & lanemask_lt());
+        L.qv[slot] = v;
+        L.qb[slot] = u;
+    }
+    L.qn += c;
+}
+
+// push_filter: claim the pairs of the level's edge frontier E[0, len) (after
+// a grid barrier that ends the advance), strided over all warps in order.
+template <int T>
+__device__ void filter_level(const Params1& p, LevelCtx& L, long long len) {
+    const long long wstride = (long long)gridDim.x * T;
+    for (long long b = (long long)blockIdx.x * T + (threadIdx.x & ~31u); b < len; b += wstride) {  // warp-uniform
+        const long long i = b + lane_id();
+        const bool has = i < len;
+        const int2 e = has ? __ldcg(p.E + i) : make_int2(0, 0);
+        claim_candidate(p, L, has, e.x, e.y);
+    }
+    flush_qbuf(L);
 }
 
 // ------------------------------------------------------------ push tiles
@@ -441,7 +513,7 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
         }
     }
     if (!units_valid || nunits == 0) {
-        flush_qbuf(L);
+        flush_push(p, L);
         return;
     }
     if (p.chunk <= T && T % p.chunk == 0 && p.chunk % 32 == 0) {
@@ -466,7 +538,7 @@ __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int d
     } else {
         for (long long it = blockIdx.x; it < nunits; it += G) push_unit<T>(p, L, __ldcg(u_cur + it));
     }
-    flush_qbuf(L);
+    flush_push(p, L);
 }
 
 // ------------------------------------------------------------ pull level

@@ -2,9 +2,11 @@
 
 Sweeps, on a given graph and seeded sources, the knobs of `bfs_options` that
 change only the schedule (never the result): drive mode, CTA size, chunk-unit
-size, warp threshold, pull flatten width, claim aggregation, and the
-direction thresholds alpha / beta / gamma; for batched (64-lane) searches the
-MS-BFS knobs.  Each candidate's mean device time per search is measured with
+size, warp threshold, pull flatten width, claim aggregation, the push
+advance / visited-update arrangement (fused, or an edge frontier claimed by a
+filter pass: Variants 13/14 and 20/23 of Section 7.2), and the direction
+thresholds alpha / beta / gamma; for batched (64-lane) searches the MS-BFS
+knobs.  Each candidate's mean device time per search is measured with
 CUDA events after warm-up; the best is stored in a JSON cache keyed by
 (GPU name, SM count, graph class, log2 n, log2 m) and returned by
 `tuned_options`.
@@ -22,7 +24,7 @@ import sys
 
 import numpy as np
 
-from . import BFS_MODE_GRAPH, BFS_MODE_PERSISTENT, Graph, options
+from . import BFS_MODE_GRAPH, BFS_MODE_PERSISTENT, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED, BFS_PUSH_FUSED, Graph, options
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(_HERE, "tune_cache.json")
@@ -34,6 +36,7 @@ SINGLE_SPACE = {
     "medium": [16, 32, 64],
     "pull_serial": [8, 16, 32],
     "claim_aggregate": [0, 1],
+    "push_filter": [BFS_PUSH_FUSED, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED],
     "alpha": [8.0, 14.0, 24.0],
     "beta": [12.0, 24.0, 48.0],
     "gamma": [8.0, 16.0, 64.0],
@@ -88,6 +91,11 @@ def time_candidate(g: Graph, sources, opt, batch: bool, reps: int = 3) -> float:
     return e0.elapsed_time(e1) * 1e3 / per
 
 
+def valid_candidate(cand: dict) -> bool:
+    """Combinations the library accepts: the filter forms need the persistent or host-loop drive."""
+    return not (cand.get("mode") == BFS_MODE_GRAPH and cand.get("push_filter", BFS_PUSH_FUSED) != BFS_PUSH_FUSED)
+
+
 def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int = 2, verbose=False):
     """Coordinate descent over `space` from the library defaults (each knob in turn)."""
     best = {}
@@ -100,7 +108,7 @@ def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int =
             for v in values:
                 cand = dict(best)
                 cand[knob] = v
-                if cand == best:
+                if cand == best or not valid_candidate(cand):
                     continue
                 t = time_candidate(g, sources, options(batch=1 if batch else 0, **cand), batch)
                 trials.append((cand, t))

@@ -215,6 +215,57 @@ def test_pull_long_row_deferral(rmat14, serial):
         _check(adj, srcs[:4], dd, pp)
 
 
+@pytest.mark.parametrize("pf", [bg.BFS_PUSH_FILTER, bg.BFS_PUSH_FILTER_PREDICATED])
+def test_push_filter_forms_match_oracle(rmat14, pf):
+    # the advance appends (target, source) pairs to an edge frontier and a
+    # filter pass after a grid barrier claims them (Variants 13/14, 20/23):
+    # push-only, the heuristic, random schedules, the host loop, small chunks
+    n, adj, g, srcs = rmat14
+    opts = [bg.options(batch=0, push_filter=pf, policy=bg.BFS_POLICY_PUSH),
+            bg.options(batch=0, push_filter=pf),
+            bg.options(batch=0, push_filter=pf, mode=bg.BFS_MODE_HOST_LOOP, chunk=64, medium=4),
+            bg.options(batch=0, push_filter=pf, block_threads=512, claim_aggregate=1)]
+    for o in opts:
+        dd, pp = _run(g, n, srcs[:4], o)
+        _check(adj, srcs[:4], dd, pp)
+    rng = np.random.default_rng(17)
+    for t in range(4):
+        sched = rng.integers(0, 3, 30).tolist()
+        s = srcs[t]
+        dd, pp = _run(g, n, [s], bg.options(schedule=sched, batch=0, push_filter=pf))
+        _check(adj, [s], dd, pp)
+
+
+@pytest.mark.parametrize("kind", ["grid", "ba", "star", "tiny"])
+def test_push_filter_other_families(kind):
+    if kind == "grid":
+        n, s, d = graphgen.grid(128, 96, 0.1, seed=4)
+    elif kind == "ba":
+        n, s, d = graphgen.barabasi_albert(1 << 14, 8, seed=8)
+    elif kind == "star":
+        n = 70000
+        s, d = np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32)
+    else:
+        n = 77
+        s = np.array([0, 1, 2, 40, 41, 76], np.int32)
+        d = np.array([1, 2, 3, 41, 42, 76], np.int32)
+    adj, g = _graph_pair(n, s, d)
+    srcs = graphgen.sample_sources(n, s, d, 3, seed=12) if kind != "tiny" else [0, 5, 40, 76]
+    for pf in (bg.BFS_PUSH_FILTER, bg.BFS_PUSH_FILTER_PREDICATED):
+        for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
+            dd, pp = _run(g, n, srcs, bg.options(batch=0, push_filter=pf, policy=pol))
+            _check(adj, srcs, dd, pp)
+
+
+def test_push_filter_option_errors(rmat14):
+    n, adj, g, srcs = rmat14
+    for o in (bg.options(batch=0, push_filter=3), bg.options(batch=0, push_filter=-1),
+              bg.options(batch=0, push_filter=bg.BFS_PUSH_FILTER, mode=bg.BFS_MODE_GRAPH)):
+        with pytest.raises(bg.BfsError) as e:
+            _run(g, n, srcs[:1], o)
+        assert e.value.status == bg.BFS_EINVAL
+
+
 def test_edge_cases_tiny_and_isolated():
     # one vertex, no edges
     g = bg.Graph.build(1, np.zeros(0, np.int32), np.zeros(0, np.int32))

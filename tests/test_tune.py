@@ -31,6 +31,20 @@ def test_coordinate_search_finds_the_separable_minimum(monkeypatch):
     assert len(trials) >= 1 + 2 + 2 + 2
 
 
+def test_coordinate_search_skips_rejected_combinations(monkeypatch):
+    # the CUDA-graph drive rejects the filter forms: never time that pair
+    def fake_time(g, sources, opt, batch, reps=3):
+        assert not (opt.mode == bg.BFS_MODE_GRAPH and opt.push_filter != bg.BFS_PUSH_FUSED)
+        return 100.0 - 20.0 * (opt.mode == bg.BFS_MODE_GRAPH) - 10.0 * (opt.push_filter == bg.BFS_PUSH_FILTER)
+
+    monkeypatch.setattr(tune, "time_candidate", fake_time)
+    space = {"mode": [bg.BFS_MODE_PERSISTENT, bg.BFS_MODE_GRAPH], "push_filter": tune.SINGLE_SPACE["push_filter"]}
+    found, t, _ = tune.coordinate_search(None, [0], space, batch=False, rounds=3)
+    assert found == {"mode": bg.BFS_MODE_GRAPH} and t == 80.0
+    assert tune.valid_candidate({"push_filter": bg.BFS_PUSH_FILTER})
+    assert not tune.valid_candidate({"mode": bg.BFS_MODE_GRAPH, "push_filter": bg.BFS_PUSH_FILTER_PREDICATED})
+
+
 def test_cache_round_trip(tmp_path, monkeypatch):
     monkeypatch.setattr(tune, "device_key", lambda: {"gpu": "TestGPU", "sms": 152})
     path = tmp_path / "cache.json"
