@@ -11,10 +11,13 @@ Functions (each follows the passage cited in ``oracle.c``):
   apsp_boolean     independent pin: Boolean matrix powers (n <= 64)
   components       independent pin: union-find
   validate         Graph500-style depth/parent checks
+  rcm, permute     Reverse Cuthill-McKee numbering (Section 7.1 preprocessing)
+                   with fixed tie breaks, and the renamed adjacency
   mlp_*, adam_step FP64 reference of the learned direction policy (no paper
                    counterpart; pinned by finite differences in the tests)
 
-Parity status: depth pinned (brute force, closed forms, invariants);
+Parity status: depth pinned (brute force, closed forms, invariants); RCM
+pinned by hand-derived orders and a declarative check of the Cuthill-McKee rules;
 parent pinned by validation (not unique); MLP pinned by finite differences.
 """
 from __future__ import annotations
@@ -60,6 +63,8 @@ def _load():
         lib.or_apsp_boolean.argtypes = [ctypes.c_int32, vp, vp]
         lib.or_apsp_boolean.restype = ctypes.c_int
         lib.or_components.argtypes = [i64, i64, vp, vp, vp]
+        lib.or_rcm.argtypes = [i64, vp, vp, vp]
+        lib.or_rcm.restype = ctypes.c_int
         lib.or_components.restype = ctypes.c_int
         lib.or_validate.argtypes = [i64, vp, vp, ctypes.c_int32, vp, vp, ctypes.c_int]
         lib.or_validate.restype = ctypes.c_int
@@ -150,6 +155,24 @@ def components(n, src, dst) -> np.ndarray:
     comp = np.empty(n, np.int32)
     _load().or_components(n, len(src), _ptr(src), _ptr(dst), _ptr(comp))
     return comp
+
+
+def rcm(adj: Adjacency) -> np.ndarray:
+    """Reverse Cuthill-McKee new id of every vertex (int32 [n]); tie rules in oracle.c."""
+    newid = np.empty(adj.n, np.int32)
+    if _load().or_rcm(adj.n, _ptr(adj.row_ptr), _ptr(adj.col), _ptr(newid)) != 0:
+        raise MemoryError("or_rcm")
+    return newid
+
+
+def permute(adj: Adjacency, newid) -> Adjacency:
+    """The same graph with vertex v renamed newid[v] (rows sorted ascending)."""
+    newid = np.asarray(newid, np.int64)
+    deg = adj.degree()
+    rows = np.repeat(np.arange(adj.n, dtype=np.int64), deg)
+    src = newid[rows].astype(np.int32)
+    dst = newid[adj.col.astype(np.int64)].astype(np.int32)
+    return build_adjacency(adj.n, src, dst, symmetrize=False, drop_self=False, dedup=False)
 
 
 def validate(adj: Adjacency, s, depth, parent=None, directed=False) -> int:

@@ -29,6 +29,10 @@
  * the component routine uses union-find: both are independent of the queue
  * BFS so that they can pin it.
  *
+ * The RCM routine numbers vertices by the Cuthill-McKee rule with fixed tie
+ * breaks (see or_rcm); the tests pin it with hand-derived orders and an
+ * independent check of the rules a Cuthill-McKee sequence must satisfy.
+ *
  * The MLP routines are the FP64 reference for the learned direction policy:
  * 10 -> 32 -> 32 -> 3 with ReLU, softmax cross-entropy averaged over rows, and
  * the Adam update of Kingma & Ba (ICLR 2015, Algorithm 1).  The paper has no
@@ -130,6 +134,73 @@ int32_t or_bfs(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t s,
     }
     free(queue);
     return maxd + 1;
+}
+
+/* ------------------------------------------------------------------ RCM */
+
+static const int64_t* rank_deg;  /* degrees seen by cmp_rank (single-threaded use) */
+
+/* rank order: degree ascending, then vertex id ascending */
+static int cmp_rank(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    int64_t dx = rank_deg[x], dy = rank_deg[y];
+    if (dx != dy) return (dx > dy) - (dx < dy);
+    return (x > y) - (x < y);
+}
+
+/*
+ * Reverse Cuthill-McKee ordering.  Section 7.1 reorders every input graph
+ * with RCM (Cuthill & McKee 1969; George & Liu).  The choices the method
+ * leaves open are fixed here so that the order is unique:
+ *   - vertices are ranked by (degree, id) ascending, degree = row length;
+ *   - each connected component starts at its lowest-ranked vertex, and the
+ *     components follow each other in the rank order of those starts;
+ *   - a vertex taken from the FIFO queue numbers its not-yet-numbered
+ *     neighbours next, in rank order (the Cuthill-McKee step);
+ *   - the whole sequence is reversed.
+ * newid[v] = n - 1 - (position of v in the Cuthill-McKee sequence).
+ * Returns 0, or -1 on allocation failure.
+ */
+int or_rcm(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* newid) {
+    int64_t* deg = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t* byrank = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    if (!deg || !byrank || !order || !pos) {
+        free(deg); free(byrank); free(order); free(pos);
+        return -1;
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = row_ptr[v + 1] - row_ptr[v];
+        byrank[v] = (int32_t)v;
+        pos[v] = -1;
+    }
+    rank_deg = deg;
+    qsort(byrank, (size_t)n, sizeof(int32_t), cmp_rank);
+    int64_t next = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t s = byrank[i];
+        if (pos[s] >= 0) continue;  /* already numbered in an earlier component */
+        pos[s] = next;
+        order[next++] = s;
+        int64_t head = pos[s];
+        while (head < next) {
+            int32_t u = order[head++];
+            int64_t first = next;
+            for (int64_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+                int32_t v = col[j];
+                if (pos[v] < 0) {
+                    pos[v] = next;
+                    order[next++] = v;
+                }
+            }
+            qsort(order + first, (size_t)(next - first), sizeof(int32_t), cmp_rank);
+            for (int64_t k = first; k < next; ++k) pos[order[k]] = k;
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) newid[v] = (int32_t)(n - 1 - pos[v]);
+    free(deg); free(byrank); free(order); free(pos);
+    return 0;
 }
 
 /*

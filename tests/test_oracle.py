@@ -335,3 +335,119 @@ def test_directed_validation_follows_edge_direction():
     assert oracle.validate(adj, 0, d, None, directed=True) == 4
     d = depth.copy(); d[3] = 5
     assert oracle.validate(adj, 0, d, None, directed=True) == 3
+
+
+# ------------------------------------------------------------------ RCM
+def _cm_rules_hold(adj, newid) -> bool:
+    """Declarative check that n-1-newid numbers the vertices in a Cuthill-McKee
+    sequence under the oracle's tie rules (rank = (degree, id)): components are
+    contiguous and start at their lowest-ranked vertex, in the rank order of the
+    starts; inside a component positions follow BFS depth from the start; inside
+    a depth level, vertices are ordered by (lowest position of a neighbour one
+    level up, rank).  Components and depths come from scipy, not from the oracle."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+    n = adj.n
+    pos = n - 1 - np.asarray(newid, np.int64)
+    if sorted(pos.tolist()) != list(range(n)):
+        return False
+    deg = adj.degree()
+    rank = np.empty(n, np.int64)
+    rank[np.lexsort((np.arange(n), deg))] = np.arange(n)
+    rows = np.repeat(np.arange(n), deg)
+    A = sp.csr_matrix((np.ones(adj.m), (rows, adj.col)), shape=(n, n))
+    ncomp, lab = cg.connected_components(A, directed=False)
+    starts = []
+    for c in range(ncomp):
+        members = np.flatnonzero(lab == c)
+        p = np.sort(pos[members])
+        if p[-1] - p[0] != len(members) - 1:
+            return False  # not contiguous
+        start = members[np.argmin(rank[members])]
+        if pos[start] != p[0]:
+            return False
+        starts.append((p[0], rank[start]))
+        dist = cg.shortest_path(A, unweighted=True, indices=int(start))
+        dm = dist[members].astype(np.int64)
+        by_pos = members[np.argsort(pos[members])]
+        if np.any(np.diff(dist[by_pos]) < 0):
+            return False  # depth must not decrease along the sequence
+        prev = None
+        for v in by_pos[1:]:
+            d = int(dist[v])
+            nb = adj.col[adj.row_ptr[v]:adj.row_ptr[v + 1]]
+            up = [pos[u] for u in nb if dist[u] == d - 1]
+            key = (d, min(up), rank[v])
+            if prev is not None and key <= prev:
+                return False
+            prev = key
+        del dm
+    starts.sort()
+    return all(starts[i][1] < starts[i + 1][1] for i in range(len(starts) - 1))
+
+
+def test_rcm_hand_derived_orders():
+    # path 3-0-4-1-2: ends 2 and 3 have degree 1, 2 ranks first; Cuthill-McKee
+    # 2,1,4,0,3 reversed
+    adj = oracle.build_adjacency(5, np.array([3, 0, 4, 1], np.int32), np.array([0, 4, 1, 2], np.int32))
+    assert oracle.rcm(adj).tolist() == [1, 3, 4, 0, 2]
+    # star 0-{1..4} plus isolated 5: CM = 5 | 1, 0, 2, 3, 4 ; reversed
+    adj = oracle.build_adjacency(6, np.zeros(4, np.int32), np.arange(1, 5, dtype=np.int32))
+    assert oracle.rcm(adj).tolist() == [3, 4, 2, 1, 0, 5]
+    # two parents: 0 (deg 1) - 1 - {2, 3}, 2 - 4, 3 - 4, 3 - 5.  CM from 0:
+    # 0, 1, {2 (deg 2), 3 (deg 3)}, then 4 (first neighbour up = 2), 5 (up = 3)
+    adj = oracle.build_adjacency(6, np.array([0, 1, 1, 2, 3, 3], np.int32), np.array([1, 2, 3, 4, 4, 5], np.int32))
+    assert oracle.rcm(adj).tolist() == [5, 4, 3, 2, 1, 0]
+
+
+def test_rcm_closed_form_path_in_natural_order():
+    n = 50
+    adj = oracle.build_adjacency(n, np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32))
+    assert np.array_equal(oracle.rcm(adj), n - 1 - np.arange(n))
+
+
+@pytest.mark.parametrize("kind", ["er", "grid", "ba", "tree", "dense"])
+def test_rcm_satisfies_the_cuthill_mckee_rules(kind):
+    rng = np.random.default_rng(4)
+    for t in range(6):
+        if kind == "er":
+            n = int(rng.integers(20, 200))
+            s, d = rng.integers(0, n, (2, int(rng.integers(n // 2, 2 * n)))).astype(np.int32)
+        elif kind == "grid":
+            n, s, d = graphgen.grid(int(rng.integers(3, 12)), int(rng.integers(3, 12)), 0.15, seed=t)
+        elif kind == "ba":
+            n, s, d = graphgen.barabasi_albert(int(rng.integers(30, 300)), 3, seed=t)
+        elif kind == "tree":
+            n = int(rng.integers(20, 300))
+            s = np.array([rng.integers(0, v) for v in range(1, n)], np.int32)
+            d = np.arange(1, n, dtype=np.int32)
+        else:
+            n = 24
+            s, d = np.array([(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.5], np.int32).T
+        adj = oracle.build_adjacency(n, s, d)
+        newid = oracle.rcm(adj)
+        assert _cm_rules_hold(adj, newid), (kind, t)
+        # the renamed graph keeps the edge set
+        padj = oracle.permute(adj, newid)
+        assert padj.m == adj.m
+        inv = np.argsort(newid)
+        for v in range(0, n, max(1, n // 7)):
+            got = np.sort(inv[padj.col[padj.row_ptr[newid[v]]:padj.row_ptr[newid[v] + 1]]])
+            assert np.array_equal(got, adj.col[adj.row_ptr[v]:adj.row_ptr[v + 1]])
+
+
+def test_rcm_rule_check_rejects_planted_mistakes():
+    # the checker must catch an unreversed sequence, a swapped tie and a bad start
+    n, s, d = graphgen.grid(6, 5, 0.1, seed=2)
+    adj = oracle.build_adjacency(n, s, d)
+    newid = oracle.rcm(adj)
+    assert _cm_rules_hold(adj, newid)
+    assert not _cm_rules_hold(adj, n - 1 - newid)  # Cuthill-McKee without the reversal
+    pos = n - 1 - newid
+    by_pos = np.argsort(pos)
+    swapped = newid.copy()
+    a, b = by_pos[3], by_pos[4]
+    swapped[a], swapped[b] = newid[b], newid[a]
+    assert not _cm_rules_hold(adj, swapped)
+    rolled = (newid + 1) % n  # start moved off the lowest-ranked vertex
+    assert not _cm_rules_hold(adj, rolled)
