@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--sources", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip batched / learned / ER extras")
+    ap.add_argument("--no-rcm", action="store_true", help="skip the Reverse Cuthill-McKee reordered leg")
     ap.add_argument("--profile-batched", type=int, default=0, metavar="R",
                     help="only run R 64-lane batched launches of the workload's sources and exit (for ncu)")
     ap.add_argument("--policy-weights", default=os.path.join(ROOT, "paper_2607_17106_gb300", "policy_weights.npy"))
@@ -86,6 +87,51 @@ def bytes_model(stats: np.ndarray, n: int):
     push = 12 * f + 4 * e_f + 4 * d_new
     pull = n / 8 + 4 * u + 4 * s_u + n / 8
     return 8.0 * n + n / 8 + float(np.minimum(push, pull).sum())
+
+
+def rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges, plain_ms, batched_ms):
+    """The paper's preprocessing (Section 7.1): the same graph renumbered in Reverse
+    Cuthill-McKee order, the same sources under the renaming; plain (one source at
+    a time) and batched device times, and the depths mapped back."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gr = bg.Graph.build(n, src, dst, flags=bg.BFS_DEFAULT_FLAGS | bg.BFS_REORDER_RCM)
+    build_s = time.perf_counter() - t0
+    newid = gr.permutation()
+    rs = newid[np.asarray(sources)].astype(np.int32)
+    k = len(rs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    single = bg.options(batch=0)
+    batched = bg.options(batch=1)
+
+    def plain():
+        for j in range(k):
+            gr.run(rs[j:j + 1], depth[j], parent[j], single)
+
+    plain()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gr.sync()
+    pms = e0.elapsed_time(e1)
+    same = bool(np.array_equal(depth.cpu().numpy()[:, newid], depth_h))
+    gr.run(rs, depth, parent, batched)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        gr.run(rs, depth, parent, batched)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gr.sync()
+    bms = e0.elapsed_time(e1) / 3
+    same = same and bool(np.array_equal(depth.cpu().numpy()[:, newid], depth_h))
+    gr.free()
+    return {"build_s_with_reorder": build_s, "plain_gteps": edges / (pms * 1e-3) / 1e9, "plain_ms_per_step": pms,
+            "plain_speedup_vs_input_order": plain_ms / pms, "batched_gteps": edges / (bms * 1e-3) / 1e9,
+            "batched_ms_per_step": bms, "batched_speedup_vs_input_order": batched_ms / bms,
+            "depth_equal_under_renaming": same}
 
 
 def teps_edges(stats: np.ndarray) -> float:
@@ -496,6 +542,9 @@ def main():
             extra["batched_learned"] = {"gteps": edges / (blms * 1e-3) / 1e9, "ms_per_step": blms,
                                         "speedup_vs_plain": ms_per_step / blms, "depth_equal_to_plain": same_depths(),
                                         "roofline_frac": float(np.sum(bmin)) / (blms * 1e-3) / 1e9 / peak}
+        if not args.no_rcm:
+            extra["rcm"] = rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges,
+                                   ms_per_step, extra["batched_msbfs"]["ms_per_step"])
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()

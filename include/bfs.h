@@ -51,7 +51,10 @@ enum {
     BFS_DEDUP = 2,      /* G is a 0/1 tensor (Eq. G): keep each (s,d) once */
     BFS_DROP_SELF = 4,  /* drop s == d */
     BFS_BUILD_CSC = 8,  /* build the d-major copy used by pull levels; aliases CSR when symmetric */
-    BFS_DEFAULT_FLAGS = 15
+    BFS_DEFAULT_FLAGS = 15,
+    BFS_REORDER_RCM = 16 /* renumber the vertices in Reverse Cuthill-McKee order (Section 7.1); needs
+                            BFS_SYMMETRIZE.  The graph then lives in the new ids: sources, depths and
+                            parents of bfs_run are new ids; bfs_graph_permutation maps them */
 };
 
 /*
@@ -64,6 +67,17 @@ enum {
  * with bfs_free_graph.  Errors: EINVAL (null pointer, n <= 0, m < 0, id
  * outside [0, n)), ERANGE (more than 2^31-1 directed entries before or after
  * deduplication), ENOMEM, ECUDA.  Synchronises `cuda_stream`.
+ *
+ * BFS_REORDER_RCM: the paper reorders every input with Reverse Cuthill-McKee
+ * (Section 7.1).  Vertices are ranked by (degree, id) in the symmetric, built
+ * CSR.  Each connected component starts at its lowest-ranked vertex, and the
+ * components follow in the rank order of their starts.  Inside a component the
+ * Cuthill-McKee sequence is built level by level on the device: a level's
+ * vertices are ordered by (lowest position of a neighbour in the previous
+ * level, rank), which is the order in which a FIFO queue that numbers each
+ * dequeued vertex's neighbours in rank order would number them.  The sequence
+ * is then reversed, and the CSR is rebuilt in the new ids.  The EINVAL case
+ * without BFS_SYMMETRIZE is added to the errors above.
  */
 bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint32_t flags,
                            void* cuda_stream, bfs_graph** out);
@@ -87,6 +101,14 @@ bfs_status bfs_graph_info(const bfs_graph* g, bfs_graph_stats* out);
  * when a destination is host memory.
  */
 bfs_status bfs_graph_csr(const bfs_graph* g, int32_t csc, int32_t* row_ptr, int32_t* col, void* cuda_stream);
+
+/*
+ * newid[v] (int32 [n], host or device) = the id in this graph of vertex v of
+ * the edge list it was built from: the Reverse Cuthill-McKee number with
+ * BFS_REORDER_RCM, v itself otherwise.  Synchronises the stream when newid is
+ * host memory.  Errors: EINVAL (null argument), ECUDA.
+ */
+bfs_status bfs_graph_permutation(const bfs_graph* g, int32_t* newid, void* cuda_stream);
 
 void bfs_free_graph(bfs_graph* g);
 

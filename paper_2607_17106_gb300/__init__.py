@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libbfsgb.so")
 BFS_OK, BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT, BFS_ERANGE, BFS_EVALIDATE = range(7)
 # build flags
 BFS_SYMMETRIZE, BFS_DEDUP, BFS_DROP_SELF, BFS_BUILD_CSC, BFS_DEFAULT_FLAGS = 1, 2, 4, 8, 15
+BFS_REORDER_RCM = 16
 # level forms
 BFS_DIR_PUSH_QUEUE, BFS_DIR_PUSH_BITMAP, BFS_DIR_PULL = 0, 1, 2
 # drive modes
@@ -36,7 +37,7 @@ BFS_MLP_IN, BFS_MLP_HIDDEN, BFS_MLP_OUT = 10, 32, 3
 BFS_MLP_NPARAM, BFS_MLP_NNORM = 1507, 20
 
 EXPORTED = [
-    "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_free_graph", "bfs_options_init", "bfs_run",
+    "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_graph_permutation", "bfs_free_graph", "bfs_options_init", "bfs_run",
     "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_level_stats_noalloc", "bfs_profile_levels",
     "bfs_policy_features", "bfs_policy_load",
     "bfs_policy_weights", "bfs_policy_free", "bfs_policy_forward", "bfs_policy_train_step",
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
         "bfs_build_graph": (st, [i32, i64, vp, vp, u32, vp, ctypes.POINTER(vp)]),
         "bfs_graph_info": (st, [vp, ctypes.POINTER(bfs_graph_stats)]),
         "bfs_graph_csr": (st, [vp, i32, vp, vp, vp]),
+        "bfs_graph_permutation": (st, [vp, vp, vp]),
         "bfs_free_graph": (None, [vp]),
         "bfs_options_init": (None, [ctypes.POINTER(bfs_options)]),
         "bfs_run": (st, [vp, vp, i32, vp, vp, ctypes.POINTER(bfs_options), vp]),
@@ -208,6 +210,12 @@ class Graph:
         col = np.empty(max(s.m, 1), np.int32)
         _check(load().bfs_graph_csr(self.handle, int(csc), _ptr(rp), _ptr(col), _stream(None)))
         return rp, col[: s.m]
+
+    def permutation(self) -> np.ndarray:
+        """bfs_graph_permutation: int32 [n], new id of every input vertex (identity unless RCM-reordered)."""
+        out = np.empty(self.n, np.int32)
+        _check(load().bfs_graph_permutation(self.handle, _ptr(out), _stream(None)))
+        return out
 
     def run(self, sources, depth, parent=None, opt: bfs_options | None = None, stream=None):
         """bfs_run: sources (int seq / array / tensor), depth/parent [k][n] buffers."""

@@ -355,6 +355,250 @@ bfs_status keys_to_csr(uint64_t* keys, int64_t count, int bits, int dedup, int32
     return BFS_OK;
 }
 
+// ------------------------------------------------------------ RCM
+// Reverse Cuthill-McKee numbering (Section 7.1), computed level by level.
+// rank(v) = position of v in (degree, id) order.  A component starts at its
+// lowest-ranked vertex; the vertices first reached from the level whose
+// positions are [lb, le) form the next level, ordered by (lowest position of
+// a neighbour in [lb, le), rank) -- the order in which a FIFO queue numbering
+// each dequeued vertex's unnumbered neighbours in rank order numbers them.
+
+constexpr int RCM_SMALL_SORT = 4096;       // levels up to this size are sorted by one CTA
+constexpr int64_t RCM_FIND_CHUNK = 1 << 20;  // rank-order window scanned per start search
+
+// key = degree << bits | v
+__global__ void rcm_rank_keys_kernel(const int32_t* row_ptr, int32_t n, int bits, uint64_t* keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(uint32_t)(row_ptr[v + 1] - row_ptr[v]) << bits) | (uint64_t)v;
+}
+
+// byrank[i] = vertex of rank i, rank[v]; pos = -1, minpos = INT32_MAX; the
+// degree-0 vertices (the lowest ranks, each its own component) are numbered
+// at once in rank order; *n0 = their count
+__global__ void rcm_init_kernel(const uint64_t* sorted, const int32_t* row_ptr, int32_t n, int bits, int32_t* byrank,
+                                int32_t* rank, int32_t* pos, int32_t* order, int32_t* minpos, int* n0) {
+    const uint64_t mask = (1ull << bits) - 1;
+    int cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)(sorted[i] & mask);
+        byrank[i] = v;
+        rank[v] = (int32_t)i;
+        minpos[v] = INT32_MAX;
+        const bool iso = row_ptr[v + 1] == row_ptr[v];
+        pos[v] = iso ? (int32_t)i : -1;
+        if (iso) order[i] = v;
+        cnt += iso ? 1 : 0;
+    }
+    cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n0, cnt);
+}
+
+// lowest rank index in [lo, hi) whose vertex is not numbered yet
+__global__ void rcm_find_start_kernel(const int32_t* byrank, const int32_t* pos, int64_t lo, int64_t hi, int* found) {
+    for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x)
+        if (pos[byrank[i]] < 0) atomicMin(found, (int)i);
+}
+
+__global__ void rcm_place_start_kernel(const int32_t* byrank, const int* found, int32_t next, int32_t* pos,
+                                       int32_t* order) {
+    const int32_t s = byrank[*found];
+    pos[s] = next;
+    order[next] = s;
+}
+
+// one warp per vertex of the level [lb, le): every unnumbered neighbour v
+// takes the lowest such position as its key and joins the next level once
+__global__ void rcm_expand_kernel(const int32_t* row_ptr, const int32_t* col, const int32_t* order, int32_t lb,
+                                  int32_t le, const int32_t* pos, int32_t* minpos, uint32_t* seen, int32_t* list,
+                                  int* cnt) {
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = lb + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); p < le; p += nwarps) {
+        const int32_t u = order[p];
+        const int32_t b = row_ptr[u], e = row_ptr[u + 1];
+        for (int32_t j = b + (int32_t)lane; j < e; j += 32) {
+            const int32_t v = col[j];
+            if (pos[v] >= 0) continue;
+            atomicMin(minpos + v, (int32_t)p);
+            const uint32_t bit = 1u << (v & 31);
+            if (!(atomicOr(seen + (v >> 5), bit) & bit)) list[atomicAdd(cnt, 1)] = v;
+        }
+    }
+}
+
+// key = minpos << bits | rank
+__global__ void rcm_level_keys_kernel(const int32_t* list, int32_t cnt, const int32_t* minpos, const int32_t* rank,
+                                      int bits, uint64_t* keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = list[i];
+        keys[i] = ((uint64_t)(uint32_t)minpos[v] << bits) | (uint64_t)(uint32_t)rank[v];
+    }
+}
+
+// ascending bitonic sort of up to RCM_SMALL_SORT keys in one CTA
+__global__ void rcm_small_sort_kernel(uint64_t* keys, int32_t cnt) {
+    __shared__ uint64_t s[RCM_SMALL_SORT];
+    for (int i = threadIdx.x; i < RCM_SMALL_SORT; i += blockDim.x) s[i] = i < cnt ? keys[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= RCM_SMALL_SORT; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < RCM_SMALL_SORT; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const uint64_t a = s[i], c = s[ixj];
+                    if ((a > c) == up) {
+                        s[i] = c;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = s[i];
+}
+
+__global__ void rcm_assign_kernel(const uint64_t* sorted, int32_t cnt, int bits, const int32_t* byrank, int32_t next,
+                                  int32_t* pos, int32_t* order) {
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = byrank[sorted[i] & mask];
+        pos[v] = next + (int32_t)i;
+        order[next + i] = v;
+    }
+}
+
+__global__ void rcm_newid_identity_kernel(int32_t n, int32_t* newid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        newid[v] = (int32_t)v;
+}
+
+__global__ void rcm_newid_kernel(const int32_t* pos, int32_t n, int32_t* newid) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        newid[v] = n - 1 - pos[v];
+}
+
+// (newid[s] << bits) | newid[d] for every CSR entry, one warp per row
+__global__ void relabel_keys_kernel(const int32_t* row_ptr, const int32_t* col, int32_t n, const int32_t* newid,
+                                    int bits, uint64_t* keys) {
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+        const uint64_t hi = (uint64_t)(uint32_t)newid[v] << bits;
+        for (int32_t j = row_ptr[v] + (int32_t)lane; j < row_ptr[v + 1]; j += 32)
+            keys[j] = hi | (uint64_t)(uint32_t)newid[col[j]];
+    }
+}
+
+template <typename T>
+bfs_status read_scalar(const T* d, T* h, cudaStream_t st) {
+    BFS_CUDA(cudaMemcpyAsync(h, d, sizeof(T), cudaMemcpyDeviceToHost, st));
+    BFS_CUDA(cudaStreamSynchronize(st));
+    return BFS_OK;
+}
+
+// newid (device [n]) of the Reverse Cuthill-McKee numbering of a symmetric CSR
+bfs_status rcm_newid(const int32_t* row_ptr, const int32_t* col, int32_t n, int bits, cudaStream_t st,
+                     int32_t* newid) {
+    Scratch sc(st);
+    uint64_t *keys, *tmp;
+    int32_t *byrank, *rank, *pos, *order, *minpos, *list;
+    uint32_t* seen;
+    int *d_n0, *d_cnt, *d_found;
+    const int64_t words = div_up(n, 32);
+    if (sc.alloc(&keys, n) || sc.alloc(&tmp, n) || sc.alloc(&byrank, n) || sc.alloc(&rank, n) || sc.alloc(&pos, n) ||
+        sc.alloc(&order, n) || sc.alloc(&minpos, n) || sc.alloc(&list, n) || sc.alloc(&seen, words) ||
+        sc.alloc(&d_n0, 1) || sc.alloc(&d_cnt, 1) || sc.alloc(&d_found, 1)) {
+        cudaGetLastError();
+        return fail(BFS_ENOMEM, "RCM scratch for n=%d", n);
+    }
+    rcm_rank_keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(row_ptr, n, bits, keys);
+    uint64_t* sorted;
+    BFS_CUDA(radix_sort_u64(keys, tmp, n, bits + 32, st, &sorted));
+    BFS_CUDA(cudaMemsetAsync(d_n0, 0, 4, st));
+    BFS_CUDA(cudaMemsetAsync(seen, 0, words * 4, st));
+    rcm_init_kernel<<<grid_for(n, 256), 256, 0, st>>>(sorted, row_ptr, n, bits, byrank, rank, pos, order, minpos, d_n0);
+    int n0 = 0;
+    bfs_status s = read_scalar(d_n0, &n0, st);
+    if (s != BFS_OK) return s;
+    int32_t next = n0;
+    int64_t cursor = n0;
+    while (cursor < n) {
+        const int64_t hi = std::min<int64_t>(n, cursor + RCM_FIND_CHUNK);
+        const int none = INT32_MAX;
+        BFS_CUDA(cudaMemcpyAsync(d_found, &none, 4, cudaMemcpyHostToDevice, st));
+        rcm_find_start_kernel<<<grid_for(hi - cursor, 256), 256, 0, st>>>(byrank, pos, cursor, hi, d_found);
+        int found = none;
+        if ((s = read_scalar(d_found, &found, st)) != BFS_OK) return s;
+        if (found == none) {
+            cursor = hi;
+            continue;
+        }
+        cursor = (int64_t)found + 1;
+        rcm_place_start_kernel<<<1, 1, 0, st>>>(byrank, d_found, next, pos, order);
+        int32_t lb = next, le = next + 1;
+        next += 1;
+        for (;;) {
+            BFS_CUDA(cudaMemsetAsync(d_cnt, 0, 4, st));
+            rcm_expand_kernel<<<grid_for((int64_t)(le - lb) * 32, 256), 256, 0, st>>>(row_ptr, col, order, lb, le, pos,
+                                                                                     minpos, seen, list, d_cnt);
+            int cnt = 0;
+            if ((s = read_scalar(d_cnt, &cnt, st)) != BFS_OK) return s;
+            if (cnt == 0) break;
+            if (next + (int64_t)cnt > n) return fail(BFS_EVALIDATE, "RCM numbered more than n vertices");
+            rcm_level_keys_kernel<<<grid_for(cnt, 256), 256, 0, st>>>(list, cnt, minpos, rank, bits, keys);
+            uint64_t* lsorted = keys;
+            if (cnt <= RCM_SMALL_SORT) {
+                rcm_small_sort_kernel<<<1, 1024, 0, st>>>(keys, cnt);
+            } else {
+                BFS_CUDA(radix_sort_u64(keys, tmp, cnt, 2 * bits, st, &lsorted));
+            }
+            rcm_assign_kernel<<<grid_for(cnt, 256), 256, 0, st>>>(lsorted, cnt, bits, byrank, next, pos, order);
+            lb = le;
+            le = next + cnt;
+            next += cnt;
+        }
+    }
+    if (next != n) return fail(BFS_EVALIDATE, "RCM numbered %d of %d vertices", next, n);
+    rcm_newid_kernel<<<grid_for(n, 256), 256, 0, st>>>(pos, n, newid);
+    BFS_CUDA(cudaGetLastError());
+    BFS_CUDA(cudaStreamSynchronize(st));
+    return BFS_OK;
+}
+
+// Renumber a built symmetric graph in RCM order: g->perm, then the CSR again
+bfs_status rcm_reorder(bfs_graph* g, int bits, cudaStream_t st) {
+    if (cudaMalloc(&g->perm, (size_t)g->n * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BFS_ENOMEM, "permutation of n=%d", g->n);
+    }
+    bfs_status s = rcm_newid(g->row_ptr, g->col, g->n, bits, st, g->perm);
+    if (s != BFS_OK) return s;
+    Scratch sc(st);
+    uint64_t* keys;
+    if (sc.alloc(&keys, g->m) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BFS_ENOMEM, "relabel keys");
+    }
+    relabel_keys_kernel<<<grid_for((int64_t)g->n * 32, 256), 256, 0, st>>>(g->row_ptr, g->col, g->n, g->perm, bits, keys);
+    BFS_CUDA(cudaGetLastError());
+    int32_t *row_ptr, *col;
+    int64_t mm = 0;
+    s = keys_to_csr(keys, g->m, bits, 0, g->n, st, &row_ptr, &col, &mm);
+    if (s != BFS_OK) return s;
+    if (mm != g->m) {
+        cudaFree(row_ptr);
+        cudaFree(col);
+        return fail(BFS_EVALIDATE, "relabelled graph has %lld entries, expected %lld", (long long)mm, (long long)g->m);
+    }
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+    g->row_ptr = g->csc_ptr = row_ptr;
+    g->col = g->csc_col = col;
+    return BFS_OK;
+}
+
 }  // namespace
 
 }  // namespace bfsgb
@@ -369,6 +613,7 @@ extern "C" bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, 
     if (m < 0) return fail(BFS_EINVAL, "m must be >= 0");
     if (m > 0 && (!src || !dst)) return fail(BFS_EINVAL, "src/dst is NULL");
     int sym = (flags & BFS_SYMMETRIZE) != 0;
+    if ((flags & BFS_REORDER_RCM) && !sym) return fail(BFS_EINVAL, "BFS_REORDER_RCM needs BFS_SYMMETRIZE");
     int64_t count = sym ? 2 * m : m;
     if (count > INT32_MAX) return fail(BFS_ERANGE, "%lld directed entries before deduplication (> 2^31-1)", (long long)count);
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -416,6 +661,13 @@ extern "C" bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, 
     if (sym) {
         g->csc_ptr = g->row_ptr;
         g->csc_col = g->col;
+        if (flags & BFS_REORDER_RCM) {
+            bfs_status sr = rcm_reorder(g, bits, st);
+            if (sr != BFS_OK) {
+                bfs_free_graph(g);
+                return sr;
+            }
+        }
     } else {
         // CSC = rank swizzle S,D -> D,S of the built CSR (already unique)
         uint64_t* tkeys;
@@ -488,5 +740,24 @@ extern "C" void bfs_free_graph(bfs_graph* g) {
     cudaFree(g->row_ptr);
     cudaFree(g->col);
     cudaFree(g->isolated);
+    cudaFree(g->perm);
     delete g;
+}
+
+extern "C" bfs_status bfs_graph_permutation(const bfs_graph* g, int32_t* newid, void* cuda_stream) {
+    if (!g || !newid) return fail(BFS_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool host = !is_device_ptr(newid);
+    if (g->perm) {
+        BFS_CUDA(cudaMemcpyAsync(newid, g->perm, (size_t)g->n * 4, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+        if (host) BFS_CUDA(cudaStreamSynchronize(st));
+        return BFS_OK;
+    }
+    if (host) {
+        for (int32_t v = 0; v < g->n; ++v) newid[v] = v;
+        return BFS_OK;
+    }
+    rcm_newid_identity_kernel<<<grid_for(g->n, 256), 256, 0, st>>>(g->n, newid);
+    BFS_CUDA(cudaGetLastError());
+    return BFS_OK;
 }

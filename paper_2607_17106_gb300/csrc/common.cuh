@@ -50,6 +50,7 @@ struct bfs_graph {
     int32_t* csc_ptr = nullptr;   // [n+1], == row_ptr when symmetric
     int32_t* csc_col = nullptr;   // [m],   == col when symmetric
     uint32_t* isolated = nullptr; // [W] bit v set iff deg(v) == 0 (out- and in-degree)
+    int32_t* perm = nullptr;      // [n] new id of each input vertex (BFS_REORDER_RCM), else null
     int32_t n_isolated = 0;
     int32_t deg_max = 0;
     double deg_mean = 0, deg_var = 0;

@@ -376,8 +376,8 @@ __device__ void filter_level(const Params1& p, LevelCtx& L, long long len) {
 
 // ------------------------------------------------------------ push tiles
 struct PullWarpSmem {
-    unsigned nb[32];                   // new bits of the block's words
-    int lv[32], lj[32], le[32], lb[32];  // deferred rows: vertex, next entry, end, row start
+    unsigned nb[32];                   // new bits of the block's words (slot = the word's lane)
+    int lv[32], lj[32], le[32], lb[32], ls[32];  // deferred rows: vertex, next entry, end, row start, slot
     int nl;
 };
 
@@ -563,11 +563,11 @@ __device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
 // F_{i+1} with plain stores (it owns them).  Warp-uniform.
 template <bool NC>
 __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
-                                                 uint32_t* f_next, long long wb, unsigned pwl) {
+                                                 uint32_t* f_next, long long bi, long long S, unsigned pwl) {
     const unsigned lane = lane_id();
     const int dnext = L.level + 1;
     const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
-    const long long wl = wb + lane;
+    const long long wl = bi + lane * S;
     if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
     unsigned todo = __ballot_sync(0xffffffffu, pwl != 0xffffffffu);
     while (todo) {
@@ -585,7 +585,7 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             unvis[k] = !((pw[k] >> lane) & 1u);
-            const long long v = (wb + wi[k]) * 32 + lane;
+            const long long v = (bi + wi[k] * S) * 32 + lane;
             beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
             end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
             j[k] = beg[k];
@@ -656,7 +656,7 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
                 }
                 rm &= rm - 1;
             }
-            const long long w = wb + wi[k];
+            const long long w = bi + wi[k] * S;
             const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
             if (lane == 0) {
                 f_next[w] = nb;
@@ -707,9 +707,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 }
 
 // Record a vertex found by a pull scan (parent u).  Any lane, any time.
-__device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWarpSmem& ws, long long wb, int v, int u,
+__device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWarpSmem& ws, int slot, int v, int u,
                                            int b0, int e) {
-    atomicOr(&ws.nb[(int)(((long long)v >> 5) - wb)], 1u << (v & 31));
+    atomicOr(&ws.nb[slot], 1u << (v & 31));
     L.depth[v] = L.level + 1;
     if (L.parent) L.parent[v] = u;
     L.ef += (unsigned long long)(p.symmetric ? (e - b0) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
@@ -718,7 +718,7 @@ __device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWa
 
 // The deferred rows of the block, each scanned by the whole warp.  Warp-uniform.
 template <bool NC>
-__device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, PullWarpSmem& ws, long long wb,
+__device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, PullWarpSmem& ws,
                                                const uint32_t* f_cur) {
     __syncwarp();
     const int nl = min(ws.nl, 32);
@@ -736,7 +736,7 @@ __device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, Pu
             const unsigned hb = __ballot_sync(0xffffffffu, h);
             if (hb) {
                 const int hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                if (lane == 0) pull_found(p, L, ws, wb, v, hit, bl, el);
+                if (lane == 0) pull_found(p, L, ws, ws.ls[r], v, hit, bl, el);
                 break;
             }
         }
@@ -750,7 +750,11 @@ constexpr int PULL_SLOTS = 2;       // vertices a lane scans at once in a sparse
 constexpr int PULL_SPARSE_MAX = 384;  // unvisited vertices (of 1024) up to which a block is sparse
 
 // Pull level (Section 5, loop order d -> s).  Warps take blocks of 32 words
-// of P (1024 vertices) round-robin.  A block with many unvisited vertices,
+// of P (1024 vertices) round-robin; block b holds the words b + l * S
+// (l = 0..31, S = the number of blocks), so each block samples the whole
+// vertex range and a cluster of costly vertices (consecutive ids in a
+// bandwidth-reducing order such as Reverse Cuthill-McKee) is spread over many
+// warps instead of landing on a few.  A block with many unvisited vertices,
 // where most scans end at their first entries, is finished two words at a
 // time (pull_block_pairs: few instructions per vertex); a block with few
 // runs the lane pipeline below, which keeps every lane busy on the long
@@ -767,8 +771,9 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int serial = max(1, min(p.pull_serial, PULL_SERIAL_MAX));
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (long long wb = gwarp * 32; wb < p.W; wb += nwarps * 32) {
-        const long long wl = wb + lane;
+    const long long S = (p.W + 31) >> 5;
+    for (long long bi = gwarp; bi < S; bi += nwarps) {
+        const long long wl = bi + lane * S;
         const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
         const unsigned um = ~pwl;  // unvisited vertices of this lane's word
         const int c = __popc(um);
@@ -785,7 +790,7 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
             continue;
         }
         if (U > PULL_SPARSE_MAX) {
-            pull_block_pairs<NC>(p, L, f_cur, f_next, wb, pwl);
+            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl);
             continue;
         }
         ws.nb[lane] = 0;
@@ -793,11 +798,11 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
         __syncwarp();
         int next = 0;  // unvisited vertices of the block handed out (warp-uniform)
         int st[PULL_SLOTS], v[PULL_SLOTS], j[PULL_SLOTS], e[PULL_SLOTS], b0[PULL_SLOTS], u[PULL_SLOTS],
-            tried[PULL_SLOTS];
+            tried[PULL_SLOTS], sl[PULL_SLOTS];
 #pragma unroll
         for (int q = 0; q < PULL_SLOTS; ++q) {
             st[q] = IDLE;
-            v[q] = j[q] = e[q] = b0[q] = u[q] = tried[q] = 0;
+            v[q] = j[q] = e[q] = b0[q] = u[q] = tried[q] = sl[q] = 0;
         }
         // every iteration advances each busy slot by one step; a vertex takes
         // at most serial + 2 steps of its slot before it ends or is deferred
@@ -818,7 +823,8 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
                     const unsigned umw = __shfl_sync(FULL, um, lo);
                     const int exw = __shfl_sync(FULL, excl, lo);
                     if (st[q] == IDLE && k < U) {
-                        v[q] = (int)((wb + lo) * 32 + nth_set_bit(umw, k - exw));
+                        v[q] = (int)((bi + lo * S) * 32 + nth_set_bit(umw, k - exw));
+                        sl[q] = lo;
                         st[q] = BOUNDS;
                         tried[q] = 0;
                     }
@@ -863,7 +869,7 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
                     st[q] = TEST;
                 } else if (st[q] == TEST) {
                     if ((x1[q] >> (u[q] & 31)) & 1u) {
-                        pull_found(p, L, ws, wb, v[q], u[q], b0[q], e[q]);
+                        pull_found(p, L, ws, sl[q], v[q], u[q], b0[q], e[q]);
                         st[q] = IDLE;
                     } else if (++j[q] >= e[q]) {
                         st[q] = IDLE;
@@ -878,13 +884,14 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
             for (int q = 0; q < PULL_SLOTS; ++q) {
                 const unsigned dm = __ballot_sync(FULL, defer[q]);
                 if (dm) {
-                    if (ws.nl + __popc(dm) > 32) pull_long_rows<NC>(p, L, ws, wb, f_cur);
+                    if (ws.nl + __popc(dm) > 32) pull_long_rows<NC>(p, L, ws, f_cur);
                     if (defer[q]) {
                         const int slot = ws.nl + __popc(dm & lanemask_lt());
                         ws.lv[slot] = v[q];
                         ws.lj[slot] = j[q];
                         ws.le[slot] = e[q];
                         ws.lb[slot] = b0[q];
+                        ws.ls[slot] = sl[q];
                         st[q] = IDLE;
                     }
                     __syncwarp();
@@ -893,7 +900,7 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
                 }
             }
         }
-        pull_long_rows<NC>(p, L, ws, wb, f_cur);
+        pull_long_rows<NC>(p, L, ws, f_cur);
         if (wl < p.W) {
             const unsigned nb = ws.nb[lane];
             f_next[wl] = nb;
