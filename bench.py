@@ -89,13 +89,14 @@ def bytes_model(stats: np.ndarray, n: int):
     return 8.0 * n + n / 8 + float(np.minimum(push, pull).sum())
 
 
-def rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges, plain_ms, batched_ms):
+def rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges, plain_ms, batched_ms,
+            extra_flags=0):
     """The paper's preprocessing (Section 7.1): the same graph renumbered in Reverse
     Cuthill-McKee order, the same sources under the renaming; plain (one source at
     a time) and batched device times, and the depths mapped back."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gr = bg.Graph.build(n, src, dst, flags=bg.BFS_DEFAULT_FLAGS | bg.BFS_REORDER_RCM)
+    gr = bg.Graph.build(n, src, dst, flags=bg.BFS_DEFAULT_FLAGS | bg.BFS_REORDER_RCM | extra_flags)
     build_s = time.perf_counter() - t0
     newid = gr.permutation()
     rs = newid[np.asarray(sources)].astype(np.int32)
@@ -545,6 +546,10 @@ def main():
         if not args.no_rcm:
             extra["rcm"] = rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges,
                                    ms_per_step, extra["batched_msbfs"]["ms_per_step"])
+            # the same with pull rows ordered by degree, highest first
+            extra["rcm_hubs_first"] = rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges,
+                                              ms_per_step, extra["batched_msbfs"]["ms_per_step"],
+                                              extra_flags=bg.BFS_PULL_HUBS_FIRST)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()

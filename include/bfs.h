@@ -52,9 +52,12 @@ enum {
     BFS_DROP_SELF = 4,  /* drop s == d */
     BFS_BUILD_CSC = 8,  /* build the d-major copy used by pull levels; aliases CSR when symmetric */
     BFS_DEFAULT_FLAGS = 15,
-    BFS_REORDER_RCM = 16 /* renumber the vertices in Reverse Cuthill-McKee order (Section 7.1); needs
-                            BFS_SYMMETRIZE.  The graph then lives in the new ids: sources, depths and
-                            parents of bfs_run are new ids; bfs_graph_permutation maps them */
+    BFS_REORDER_RCM = 16, /* renumber the vertices in Reverse Cuthill-McKee order (Section 7.1); needs
+                             BFS_SYMMETRIZE.  The graph then lives in the new ids: sources, depths and
+                             parents of bfs_run are new ids; bfs_graph_permutation maps them */
+    BFS_PULL_HUBS_FIRST = 32 /* order each d-major row by the degree of its entries, highest first (ties by
+                                id), instead of by id; pull scans then meet likely frontier vertices first
+                                whatever the numbering.  Symmetric graphs get a second column array */
 };
 
 /*
@@ -78,6 +81,13 @@ enum {
  * dequeued vertex's neighbours in rank order would number them.  The sequence
  * is then reversed, and the CSR is rebuilt in the new ids.  The EINVAL case
  * without BFS_SYMMETRIZE is added to the errors above.
+ *
+ * BFS_PULL_HUBS_FIRST: a pull scan (Section 5) may stop at any in-neighbour in
+ * F_i, since the ANY of Eq. advance picks one.  A high-degree in-neighbour is
+ * the most likely to be in F_i, so rows of the d-major copy are ordered by the
+ * entry's out-degree, descending, ties by id.  Depths are unchanged; the
+ * parent chosen is the first frontier entry in this order.  The CSR keeps
+ * ascending rows, and the level statistics are taken on it.
  */
 bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, uint32_t flags,
                            void* cuda_stream, bfs_graph** out);
@@ -232,7 +242,12 @@ bfs_status bfs_run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const
  * |F_i|, degree sum over F_i, non-isolated vertices unvisited before level i,
  * CSR entries a pull level reads (each unvisited row scanned in ascending
  * order up to its first neighbour of depth i, or fully; Section 5), |F_{i+1}|
- * and the degree sum over the unvisited vertices.  depth[n]: host or device
+ * and the degree sum over the unvisited vertices.  s_u is computed in closed
+ * form: a row is read fully at every level before the one that finds its
+ * vertex, and up to the first neighbour one level up at that level.  This is
+ * exact for symmetric graphs, where no neighbour lies more than one level
+ * away.  For a directed graph it is an upper bound, and a pull level there
+ * scans in-rows instead.  depth[n]: host or device
  * output of bfs_run for one source.  stats: host array of 6*max_levels int64.
  * *levels receives L.  Errors: EINVAL, ERANGE (L > max_levels).  Synchronises.
  */

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libbfsgb.so")
 BFS_OK, BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT, BFS_ERANGE, BFS_EVALIDATE = range(7)
 # build flags
 BFS_SYMMETRIZE, BFS_DEDUP, BFS_DROP_SELF, BFS_BUILD_CSC, BFS_DEFAULT_FLAGS = 1, 2, 4, 8, 15
-BFS_REORDER_RCM = 16
+BFS_REORDER_RCM, BFS_PULL_HUBS_FIRST = 16, 32
 # level forms
 BFS_DIR_PUSH_QUEUE, BFS_DIR_PUSH_BITMAP, BFS_DIR_PULL = 0, 1, 2
 # drive modes

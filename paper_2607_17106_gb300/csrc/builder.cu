@@ -567,6 +567,78 @@ bfs_status rcm_newid(const int32_t* row_ptr, const int32_t* col, int32_t n, int 
     return BFS_OK;
 }
 
+// ------------------------------------------------------------ hubs-first rows
+// key = (INT32_MAX - degree) << bits | v: ascending = degree descending, id ascending
+__global__ void hub_rank_keys_kernel(const int32_t* row_ptr, int32_t n, int bits, uint64_t* keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(uint32_t)(INT32_MAX - (row_ptr[v + 1] - row_ptr[v])) << bits) | (uint64_t)v;
+}
+
+__global__ void rank_of_kernel(const uint64_t* sorted, int32_t n, int bits, int32_t* byrank, int32_t* rank) {
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)(sorted[i] & mask);
+        byrank[i] = v;
+        rank[v] = (int32_t)i;
+    }
+}
+
+// (row << bits) | rank of the entry, one warp per row
+__global__ void hub_row_keys_kernel(const int32_t* ptr, const int32_t* col, int32_t n, const int32_t* rank, int bits,
+                                    uint64_t* keys) {
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps)
+        for (int32_t j = ptr[v] + (int32_t)lane; j < ptr[v + 1]; j += 32)
+            keys[j] = ((uint64_t)v << bits) | (uint64_t)(uint32_t)rank[col[j]];
+}
+
+__global__ void hub_col_kernel(const uint64_t* sorted, int64_t m, int bits, const int32_t* byrank, int32_t* col) {
+    const uint64_t mask = (1ull << bits) - 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        col[j] = byrank[sorted[j] & mask];
+}
+
+// Replace the d-major column array by one whose rows are ordered by the
+// entries' out-degree, highest first (ties by id); row bounds are unchanged.
+bfs_status pull_hubs_first(bfs_graph* g, int bits, cudaStream_t st) {
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    Scratch sc(st);
+    uint64_t *rk, *rt, *keys, *tmp;
+    int32_t *byrank, *rank, *col;
+    if (sc.alloc(&rk, n) || sc.alloc(&rt, n) || sc.alloc(&byrank, n) || sc.alloc(&rank, n) || sc.alloc(&keys, m) ||
+        sc.alloc(&tmp, m)) {
+        cudaGetLastError();
+        return fail(BFS_ENOMEM, "hubs-first scratch");
+    }
+    if (cudaMalloc(&col, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BFS_ENOMEM, "hubs-first column array of %lld entries", (long long)m);
+    }
+    hub_rank_keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(g->row_ptr, n, bits, rk);
+    uint64_t* rs;
+    cudaError_t e = radix_sort_u64(rk, rt, n, bits + 32, st, &rs);
+    if (e == cudaSuccess) {
+        rank_of_kernel<<<grid_for(n, 256), 256, 0, st>>>(rs, n, bits, byrank, rank);
+        hub_row_keys_kernel<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(g->csc_ptr, g->csc_col, n, rank, bits, keys);
+        uint64_t* ks;
+        e = radix_sort_u64(keys, tmp, m, 2 * bits, st, &ks);
+        if (e == cudaSuccess) {
+            hub_col_kernel<<<grid_for(m, 256), 256, 0, st>>>(ks, m, bits, byrank, col);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(col);
+        return cuda_fail(e, "hubs-first rows");
+    }
+    if (g->csc_col != g->col) cudaFree(g->csc_col);
+    g->csc_col = col;
+    return BFS_OK;
+}
+
 // Renumber a built symmetric graph in RCM order: g->perm, then the CSR again
 bfs_status rcm_reorder(bfs_graph* g, int bits, cudaStream_t st) {
     if (cudaMalloc(&g->perm, (size_t)g->n * sizeof(int32_t)) != cudaSuccess) {
@@ -681,6 +753,13 @@ extern "C" bfs_status bfs_build_graph(int32_t n, int64_t m, const int32_t* src, 
         if (s2 != BFS_OK) {
             bfs_free_graph(g);
             return s2;
+        }
+    }
+    if (flags & BFS_PULL_HUBS_FIRST) {
+        bfs_status sh = pull_hubs_first(g, bits, st);
+        if (sh != BFS_OK) {
+            bfs_free_graph(g);
+            return sh;
         }
     }
     int64_t words = div_up(n, 32);

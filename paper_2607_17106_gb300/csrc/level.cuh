@@ -635,19 +635,23 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
                 const int l = __ffs(rm) - 1;
                 const int bl = __shfl_sync(0xffffffffu, j[k], l);
                 const int el = __shfl_sync(0xffffffffu, end[k], l);
+                // 4 x 32 entries a step, all column loads issued before the
+                // frontier tests; the first hit in row order is the parent
                 int hit = -1;
-                for (int base = bl; base < el; base += 32) {
-                    const int idx = base + (int)lane;
-                    int uu = 0;
-                    bool h = false;
-                    if (idx < el) {
-                        uu = __ldg(p.csc_col + idx);
-                        h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+                for (int base = bl; base < el && hit < 0; base += 128) {
+                    int uu[4];
+                    unsigned fw[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int idx = base + q * 32 + (int)lane;
+                        uu[q] = idx < el ? __ldg(p.csc_col + idx) : -1;
                     }
-                    const unsigned hb = __ballot_sync(0xffffffffu, h);
-                    if (hb) {
-                        hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                        break;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const unsigned hb = __ballot_sync(0xffffffffu, uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u));
+                        if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[q], __ffs(hb) - 1);
                     }
                 }
                 if ((int)lane == l && hit >= 0) {

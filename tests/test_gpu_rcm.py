@@ -108,3 +108,60 @@ def test_rcm_errors_and_identity_permutation():
     bg.load().bfs_graph_permutation(gr.handle, bg._ptr(out), bg._stream(None))
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), gr.permutation())
+
+
+# ------------------------------------------------------- hubs-first pull rows
+def _hubs_first_rows(adjt, outdeg):
+    """Rows of the d-major adjacency ordered by the entry's out-degree, descending, ties by id."""
+    cols = []
+    for v in range(adjt.n):
+        row = adjt.col[adjt.row_ptr[v]:adjt.row_ptr[v + 1]]
+        cols.append(row[np.lexsort((row, -outdeg[row]))])
+    return np.concatenate(cols) if cols else np.zeros(0, np.int32)
+
+
+@pytest.mark.parametrize("kind", ["rmat14", "ba", "grid", "directed", "rcm"])
+def test_pull_hubs_first_rows_and_bfs(kind):
+    directed = kind == "directed"
+    if directed:
+        n, s, d = graphgen.rmat(12, 8, seed=21)
+        flags = bg.BFS_DEDUP | bg.BFS_DROP_SELF | bg.BFS_BUILD_CSC | bg.BFS_PULL_HUBS_FIRST
+        adj = oracle.build_adjacency(n, s, d, symmetrize=False)
+        adjt = oracle.build_adjacency(n, d, s, symmetrize=False)
+    else:
+        n, s, d = _graph("rmat14" if kind == "rcm" else kind)
+        flags = RCM_FLAGS | bg.BFS_PULL_HUBS_FIRST if kind == "rcm" else bg.BFS_DEFAULT_FLAGS | bg.BFS_PULL_HUBS_FIRST
+        adj = oracle.build_adjacency(n, s, d)
+        if kind == "rcm":
+            adj = oracle.permute(adj, oracle.rcm(adj))
+        adjt = adj
+    g = bg.Graph.build(n, s, d, flags=flags)
+    rp, col = g.csr()
+    assert np.array_equal(rp.astype(np.int64), adj.row_ptr) and np.array_equal(col, adj.col)  # CSR ascending
+    rpt, colt = g.csr(csc=True)
+    assert np.array_equal(rpt.astype(np.int64), adjt.row_ptr)
+    assert np.array_equal(colt, _hubs_first_rows(adjt, adj.degree()))
+    newid = g.permutation()
+    srcs = newid[np.asarray(graphgen.sample_sources(n, s, d, 4, seed=23))]
+    opts = [bg.options(batch=0), bg.options(batch=0, policy=bg.BFS_POLICY_PULL),
+            bg.options(batch=0, policy=bg.BFS_POLICY_PULL, mode=bg.BFS_MODE_GRAPH), bg.options(batch=1),
+            bg.options(batch=1, policy=bg.BFS_POLICY_PULL)]
+    for o in opts:
+        depth = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        parent = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+        g.run(srcs, depth, parent, o)
+        g.sync()
+        dd, pp = depth.cpu().numpy(), parent.cpu().numpy()
+        for j, sj in enumerate(srcs):
+            ref, _ = oracle.bfs(adj, int(sj), with_parent=False)
+            assert np.array_equal(dd[j], ref)
+            assert oracle.validate(adj, int(sj), dd[j], pp[j], directed=directed) == 0
+    if directed:
+        return  # the statistics' closed form for s_u is exact on symmetric graphs only
+    # level statistics stay those of the ascending rows
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.run(srcs[:1], depth, None, bg.options(batch=0))
+    g.sync()
+    got = g.level_stats(depth)
+    want = oracle.level_stats(adj, depth.cpu().numpy())
+    assert np.array_equal(got, want)
