@@ -59,6 +59,24 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_source_seed(base_seed: int, rank: int) -> int:
+    """Seed of a rank's sources: every replica searches its own seeded sources (weak scaling)."""
+    return base_seed + 1000 * rank
+
+
+def replica_totals(dist, edges: float, seconds: float, device="cpu"):
+    """Whole-job totals of a replicas-only run: the edges all ranks traversed
+    (sum) and the slowest rank's time (max).  dist = None on one process."""
+    if dist is None:
+        return float(edges), float(seconds)
+    import torch
+    e = torch.tensor([float(edges)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(e.item()), float(t.item())
+
+
 def describe(w) -> str:
     p = w.params
     if w.kind == "rmat":
@@ -296,7 +314,7 @@ def run_reference(args):
 MIXED = "mixed-rmat16-22-q256"
 
 
-def run_mixed_bench(args, bg, torch):
+def run_mixed_bench(args, bg, torch, dist=None, rank=0, ws=1):
     """256 queries over RMAT graphs of scales 16..22 (edge factor 16, seeds 16..22),
     the graph of each query drawn uniformly (seed 106): one bfs_run_mixed launch
     against the same queries as per-graph 64-lane batches and one at a time."""
@@ -331,12 +349,17 @@ def run_mixed_bench(args, bg, torch):
     for i, gi in enumerate(goq):
         st = gl[gi].level_stats(depth[i])
         edges += teps_edges(st)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         mixed_once()
     e1.record(stream)
     torch.cuda.synchronize()
     ms_mixed = e0.elapsed_time(e1) / args.steps
+    # replicas: every rank runs the same 256 queries
+    job_edges, ms_mixed = replica_totals(dist, edges, ms_mixed, "cuda")
     ok = all(np.array_equal(depth[i].cpu().numpy(), ref[i]) for i in range(q))
     # the same queries per graph as ordinary 64-lane batches, and one at a time
     e0.record(stream)
@@ -356,8 +379,10 @@ def run_mixed_bench(args, bg, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_single = e0.elapsed_time(e1)
+    if rank != 0:
+        return 0
     line = {"metric": "BFS GTEPS, mixed batch of 256 queries over RMAT scales 16-22 in one persistent launch",
-            "value": edges / (ms_mixed * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+            "value": job_edges / (ms_mixed * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": MIXED + ": 256 queries, graph of each uniform over RMAT scales 16..22 (edge "
@@ -388,12 +413,15 @@ def main():
     bg.load()
     stream = torch.cuda.current_stream()
     if args.workload == MIXED:
-        return run_mixed_bench(args, bg, torch)
+        rc = run_mixed_bench(args, bg, torch, dist, rank, ws)
+        if dist:
+            dist.destroy_process_group()
+        return rc
 
     w = graphgen.WORKLOADS[args.workload]
     n, src, dst = w.edges()
     # weak scaling: every rank searches its own 64 seeded sources on a replica
-    sources = graphgen.sample_sources(n, src, dst, args.sources, w.source_seed + 1000 * rank)
+    sources = graphgen.sample_sources(n, src, dst, args.sources, rank_source_seed(w.source_seed, rank))
     g = bg.Graph.build(n, src, dst)
     info = g.info()
     k = len(sources)
@@ -446,12 +474,10 @@ def main():
     g.sync()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(args.steps) for j in range(k)]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # every rank searched its own sources: the job's edges over the slowest rank's time
+    job_edges, total_ms = replica_totals(dist, edges, total_ms, "cuda")
     ms_per_step = total_ms / args.steps
-    value = ws * edges / (ms_per_step * 1e-3) / 1e9
+    value = job_edges / (ms_per_step * 1e-3) / 1e9
 
     peak, peak_kind = measured_peak()
     mean_launch_s = float(np.mean(launch_ms)) * 1e-3
@@ -557,12 +583,15 @@ def main():
     parent_host = torch.empty((k, n), dtype=torch.int32).pin_memory()
     e2e_steps = max(1, min(args.steps, 2))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         g.run(src_host, depth_host, parent_host, opt)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ws * edges / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
+    job_edges_e2e, e2e_s = replica_totals(dist, edges, e2e_s, "cuda")
+    e2e = {"value": job_edges_e2e / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
            "d2h_bytes_per_step": 8 * k * n, "ms_per_step": e2e_s * 1e3,
            "path": "bfs_run(k=64, host sources, host depth/parent, one source at a time)"}
 
