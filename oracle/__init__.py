@@ -11,6 +11,8 @@ Functions (each follows the passage cited in ``oracle.c``):
   apsp_boolean     independent pin: Boolean matrix powers (n <= 64)
   components       independent pin: union-find
   validate         Graph500-style depth/parent checks
+  min_label        connected components as the fixed point of min-label
+                   propagation (the min operator in place of ANY)
   rcm, permute     Reverse Cuthill-McKee numbering (Section 7.1 preprocessing)
                    with fixed tie breaks, and the renamed adjacency
   mlp_*, adam_step FP64 reference of the learned direction policy (no paper
@@ -64,6 +66,8 @@ def _load():
         lib.or_apsp_boolean.restype = ctypes.c_int
         lib.or_components.argtypes = [i64, i64, vp, vp, vp]
         lib.or_rcm.argtypes = [i64, vp, vp, vp]
+        lib.or_min_label.argtypes = [i64, vp, vp, vp]
+        lib.or_min_label.restype = ctypes.c_int
         lib.or_rcm.restype = ctypes.c_int
         lib.or_components.restype = ctypes.c_int
         lib.or_validate.argtypes = [i64, vp, vp, ctypes.c_int32, vp, vp, ctypes.c_int]
@@ -155,6 +159,14 @@ def components(n, src, dst) -> np.ndarray:
     comp = np.empty(n, np.int32)
     _load().or_components(n, len(src), _ptr(src), _ptr(dst), _ptr(comp))
     return comp
+
+
+def min_label(adj: Adjacency) -> np.ndarray:
+    """Fixed point of min-label propagation: smallest vertex id of each vertex's component (int32 [n])."""
+    label = np.empty(adj.n, np.int32)
+    if _load().or_min_label(adj.n, _ptr(adj.row_ptr), _ptr(adj.col), _ptr(label)) != 0:
+        raise MemoryError("or_min_label")
+    return label
 
 
 def rcm(adj: Adjacency) -> np.ndarray:

@@ -136,6 +136,44 @@ int32_t or_bfs(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t s,
     return maxd + 1;
 }
 
+/* ------------------------------------------------- min-label components */
+
+/*
+ * Connected components with the min operator of the paper's operator table
+ * in place of ANY: starting from L_0[v] = v, the cascade
+ *   L_{i+1}[d] = min(L_i[d], min over s adjacent to d of L_i[s])
+ * reaches a fixed point in which every vertex holds the smallest id of its
+ * component.  That fixed point is written out directly here: vertices are
+ * visited in ascending id order, and each one not yet labelled labels its
+ * whole component, found by a FIFO search, with its own id.  This is the
+ * smallest id there, because every smaller id was reached earlier from a
+ * smaller start.
+ * The adjacency must be symmetric.  Returns 0, or -1 on allocation failure.
+ */
+int or_min_label(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* label) {
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!queue) return -1;
+    for (int64_t v = 0; v < n; ++v) label[v] = -1;
+    for (int64_t s = 0; s < n; ++s) {
+        if (label[s] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        label[s] = (int32_t)s;
+        queue[tail++] = (int32_t)s;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int64_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+                int32_t v = col[j];
+                if (label[v] < 0) {
+                    label[v] = (int32_t)s;
+                    queue[tail++] = v;
+                }
+            }
+        }
+    }
+    free(queue);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ RCM */
 
 static const int64_t* rank_deg;  /* degrees seen by cmp_rank (single-threaded use) */

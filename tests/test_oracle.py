@@ -451,3 +451,39 @@ def test_rcm_rule_check_rejects_planted_mistakes():
     assert not _cm_rules_hold(adj, swapped)
     rolled = (newid + 1) % n  # start moved off the lowest-ranked vertex
     assert not _cm_rules_hold(adj, rolled)
+
+
+# ------------------------------------------------------------ min-label components
+def test_min_label_closed_forms():
+    # path, a cycle plus isolated vertices, two stars: smallest id per component
+    adj = oracle.build_adjacency(6, np.array([5, 4, 3, 2, 1], np.int32), np.array([4, 3, 2, 1, 0], np.int32))
+    assert oracle.min_label(adj).tolist() == [0] * 6
+    adj = oracle.build_adjacency(8, np.array([3, 5, 7], np.int32), np.array([5, 7, 3], np.int32))
+    assert oracle.min_label(adj).tolist() == [0, 1, 2, 3, 4, 3, 6, 3]
+    adj = oracle.build_adjacency(7, np.array([6, 6, 2, 2], np.int32), np.array([4, 5, 0, 1], np.int32))
+    assert oracle.min_label(adj).tolist() == [0, 0, 0, 3, 4, 4, 4]
+
+
+@pytest.mark.parametrize("kind", ["er", "grid", "rmat", "ba"])
+def test_min_label_equals_union_find_and_scipy(kind):
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+    rng = np.random.default_rng(8)
+    for t in range(4):
+        if kind == "er":
+            n = int(rng.integers(50, 3000))
+            s, d = rng.integers(0, n, (2, int(rng.integers(n // 3, n)))).astype(np.int32)
+        elif kind == "grid":
+            n, s, d = graphgen.grid(int(rng.integers(5, 60)), int(rng.integers(5, 60)), 0.45, seed=t)
+        elif kind == "rmat":
+            n, s, d = graphgen.rmat(11, 2, seed=30 + t)
+        else:
+            n, s, d = graphgen.barabasi_albert(2000, 1, seed=t)
+        adj = oracle.build_adjacency(n, s, d)
+        lab = oracle.min_label(adj)
+        assert np.array_equal(lab, oracle.components(n, s, d))  # union-find, separate code
+        A = sp.csr_matrix((np.ones(adj.m), (np.repeat(np.arange(n), adj.degree()), adj.col)), shape=(n, n))
+        _, comp = cg.connected_components(A, directed=False)
+        first = np.full(comp.max() + 1, n)
+        np.minimum.at(first, comp, np.arange(n))
+        assert np.array_equal(lab, first[comp])  # scipy components, smallest id each
