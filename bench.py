@@ -577,6 +577,22 @@ def main():
                                               ms_per_step, extra["batched_msbfs"]["ms_per_step"],
                                               extra_flags=bg.BFS_PULL_HUBS_FIRST)
 
+    if not args.no_extra:
+        # connected components by min-label propagation on the same graph
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.components(lab)
+        times, iters = [], 0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, iters = g.components(lab)  # synchronises
+            times.append(time.perf_counter() - t0)
+        cms = float(np.median(times)) * 1e3
+        extra["components"] = {"ms": cms, "iterations": iters,
+                               "gteps": info.m / 2 / (cms * 1e-3) / 1e9,
+                               "components": int(torch.unique(lab).numel()),
+                               "timer": "host, around the synchronous bfs_components call"}
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     src_host = torch.from_numpy(np.asarray(sources, np.int32)).pin_memory()
     depth_host = torch.empty((k, n), dtype=torch.int32).pin_memory()

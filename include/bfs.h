@@ -274,6 +274,21 @@ bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max
 bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
                                    int32_t* levels, void* cuda_stream);
 
+/*
+ * Connected components by min-label propagation.  This is the cascade of
+ * Cascade 1 over the same graph tensor with the min operator of the paper's
+ * operator table (Section 2) in place of ANY: L_0[v] = v, F_0 = the vertices
+ * with an edge, L_{i+1}[d] = min(L_i[d], min over s in F_i adjacent to d of
+ * L_i[s]), F_{i+1} = the vertices whose label dropped, stop when F_{i+1} is
+ * empty.  label[v] (int32 [n], host or device) receives the smallest vertex id
+ * of v's connected component.  *iterations (host, may be NULL) receives the
+ * number of iterations run.  One cooperative launch, no host work per
+ * iteration.  The graph must be symmetric (built with BFS_SYMMETRIZE).
+ * Synchronises `cuda_stream`.  Errors: EINVAL (null argument, directed graph,
+ * wrong device), ENOMEM, ECUDA, ETIMEOUT.
+ */
+bfs_status bfs_components(const bfs_graph* g, int32_t* label, int32_t* iterations, void* cuda_stream);
+
 /* ----------------------------------------------------- learned policy (MLP) */
 /*
  * Direction policy: an FP32 MLP 10 -> 32 -> 32 -> 3 (ReLU) whose argmax picks

@@ -37,7 +37,8 @@ BFS_MLP_IN, BFS_MLP_HIDDEN, BFS_MLP_OUT = 10, 32, 3
 BFS_MLP_NPARAM, BFS_MLP_NNORM = 1507, 20
 
 EXPORTED = [
-    "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_graph_permutation", "bfs_free_graph", "bfs_options_init", "bfs_run",
+    "bfs_build_graph", "bfs_graph_info", "bfs_graph_csr", "bfs_graph_permutation", "bfs_components",
+    "bfs_free_graph", "bfs_options_init", "bfs_run",
     "bfs_sync", "bfs_run_mixed", "bfs_level_stats", "bfs_level_stats_noalloc", "bfs_profile_levels",
     "bfs_policy_features", "bfs_policy_load",
     "bfs_policy_weights", "bfs_policy_free", "bfs_policy_forward", "bfs_policy_train_step",
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
         "bfs_graph_info": (st, [vp, ctypes.POINTER(bfs_graph_stats)]),
         "bfs_graph_csr": (st, [vp, i32, vp, vp, vp]),
         "bfs_graph_permutation": (st, [vp, vp, vp]),
+        "bfs_components": (st, [vp, vp, vp, vp]),
         "bfs_free_graph": (None, [vp]),
         "bfs_options_init": (None, [ctypes.POINTER(bfs_options)]),
         "bfs_run": (st, [vp, vp, i32, vp, vp, ctypes.POINTER(bfs_options), vp]),
@@ -210,6 +212,13 @@ class Graph:
         col = np.empty(max(s.m, 1), np.int32)
         _check(load().bfs_graph_csr(self.handle, int(csc), _ptr(rp), _ptr(col), _stream(None)))
         return rp, col[: s.m]
+
+    def components(self, label=None, stream=None):
+        """bfs_components: (label [n] int32, iterations); label host numpy (default) or a device tensor."""
+        out = np.empty(self.n, np.int32) if label is None else label
+        it = ctypes.c_int32(0)
+        _check(load().bfs_components(self.handle, _ptr(out), ctypes.byref(it), _stream(stream)))
+        return out, it.value
 
     def permutation(self) -> np.ndarray:
         """bfs_graph_permutation: int32 [n], new id of every input vertex (identity unless RCM-reordered)."""

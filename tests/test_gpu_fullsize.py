@@ -100,3 +100,11 @@ def test_reordered_full_size_sampled(full):
     ref, _ = oracle.bfs(adj, int(srcs[j]), with_parent=False)
     assert np.array_equal(depth.cpu().numpy()[newid], ref), name
     gr.free()
+
+
+def test_components_full_size(full):
+    name, n, s, d, srcs, g, adj = full
+    got, iters = g.components()
+    assert np.array_equal(got, oracle.min_label(adj)), name
+    assert iters > 0
+
