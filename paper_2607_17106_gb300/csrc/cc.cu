@@ -125,17 +125,17 @@ __device__ __forceinline__ void cc_count(CountersCC* nxt, unsigned long long cnt
     __syncthreads();
 }
 
-// d's label dropped to lv (it owns the store or won the atomic): record it in F_{i+1}
+// d's label dropped (this thread's atomic lowered it): record d in F_{i+1}
 __device__ __forceinline__ void cc_mark(uint32_t* f_nxt, int d, unsigned long long& cnt) {
     const unsigned bit = 1u << (d & 31);
     if (!(atomicOr(f_nxt + (d >> 5), bit) & bit)) cnt += 1;
 }
 
 // Pull iteration.  Units left by a push iteration are expanded in push form
-// first (their rows were in F_{i-1}); then the fixed units of the big rows
-// each give a CTA-wide minimum, and warps take the words of all vertices,
-// each word's rows below CC_CHUNK flattened over the warp.  F_i is consumed
-// (cleared) because a pull reads every neighbour anyway.
+// first (their rows were in F_{i-1}); then each fixed unit of a big row gives
+// a warp-wide minimum, and warps take the words of all vertices, each word's
+// rows below CC_CHUNK flattened over the warp.  F_i is consumed (cleared)
+// because a pull reads every neighbour anyway.
 template <int T>
 __device__ void cc_pull(const ParamsCC& p, uint32_t* f_cur, uint32_t* f_nxt, const int2* u_cur,
                         long long nunits, long long n_big, unsigned long long& cnt) {
@@ -165,66 +165,66 @@ __device__ void cc_pull(const ParamsCC& p, uint32_t* f_cur, uint32_t* f_nxt, con
     const long long per = (p.W + nwarps - 1) / nwarps;
     const long long iend = min((gwarp + 1) * per, (long long)p.W);
     for (long long i0 = gwarp * per; i0 < iend; i0 += 32) {  // 32 words of the dealing order a step
-    const long long il = i0 + (long long)lane;
-    const long long wl = il < iend ? cc_word(p, il) : -1;
-    if (wl >= 0 && __ldcg(f_cur + wl)) f_cur[wl] = 0u;  // the buffer holds F_{i+2} next
-    for (unsigned todo = __ballot_sync(0xffffffffu, wl >= 0); todo; todo &= todo - 1) {  // warp-uniform
-        const long long w = __shfl_sync(0xffffffffu, wl, __ffs(todo) - 1);
-        const int d = (int)(w * 32 + lane);
-        int beg = 0, deg = 0, ld = INT32_MAX;
-        if (d < p.n) {
-            beg = __ldg(p.row_ptr + d);
-            deg = __ldg(p.row_ptr + d + 1) - beg;
-            ld = __ldcg(p.label + d);
-        }
-        const int fdeg = deg < CC_CHUNK ? deg : 0;
-        int incl = fdeg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        const int excl = incl - fdeg;
-        int mine = INT32_MAX;  // minimum over this lane's row
-        for (int base = 0; base < total; base += 32) {
-            const int idx = base + (int)lane;
-            int o = 0;
-#pragma unroll
-            for (int st = 16; st > 0; st >>= 1) {
-                const int ex = __shfl_sync(0xffffffffu, excl, (o + st) & 31);
-                if (o + st < 32 && ex <= idx) o += st;
+        const long long il = i0 + (long long)lane;
+        const long long wl = il < iend ? cc_word(p, il) : -1;
+        if (wl >= 0 && __ldcg(f_cur + wl)) f_cur[wl] = 0u;  // the buffer holds F_{i+2} next
+        for (unsigned todo = __ballot_sync(0xffffffffu, wl >= 0); todo; todo &= todo - 1) {  // warp-uniform
+            const long long w = __shfl_sync(0xffffffffu, wl, __ffs(todo) - 1);
+            const int d = (int)(w * 32 + lane);
+            int beg = 0, deg = 0, ld = INT32_MAX;
+            if (d < p.n) {
+                beg = __ldg(p.row_ptr + d);
+                deg = __ldg(p.row_ptr + d + 1) - beg;
+                ld = __ldcg(p.label + d);
             }
-            const int ob = __shfl_sync(0xffffffffu, beg, o);
-            const int oex = __shfl_sync(0xffffffffu, excl, o);
-            const int val = idx < total ? __ldcg(p.label + __ldg(p.col + ob + (idx - oex))) : INT32_MAX;
-            // segmented minimum: owners are non-decreasing over the lanes, so
-            // each lane keeps the minimum of its owner's entries in this step
-            int segmin = val;
+            const int fdeg = deg < CC_CHUNK ? deg : 0;
+            int incl = fdeg;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_down_sync(0xffffffffu, segmin, off);
-                const int oy = __shfl_down_sync(0xffffffffu, o, off);
-                if ((int)lane + off < 32 && oy == o) segmin = min(segmin, y);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += y;
             }
-            // the first lane of each owner's run holds its minimum; hand it to the owner
-            const int op = __shfl_up_sync(0xffffffffu, o, 1);
-            const bool head = idx < total && (lane == 0 || op != o);
-            const unsigned hm = __ballot_sync(0xffffffffu, head);
-            // owner lane L takes the value of the head lane whose o == L (at most one per step)
-            for (unsigned h = hm; h; h &= h - 1) {
-                const int hl = __ffs(h) - 1;
-                const int ho = __shfl_sync(0xffffffffu, o, hl);
-                const int hv = __shfl_sync(0xffffffffu, segmin, hl);
-                if ((int)lane == ho) mine = min(mine, hv);
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            const int excl = incl - fdeg;
+            int mine = INT32_MAX;  // minimum over this lane's row
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + (int)lane;
+                int o = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, (o + st) & 31);
+                    if (o + st < 32 && ex <= idx) o += st;
+                }
+                const int ob = __shfl_sync(0xffffffffu, beg, o);
+                const int oex = __shfl_sync(0xffffffffu, excl, o);
+                const int val = idx < total ? __ldcg(p.label + __ldg(p.col + ob + (idx - oex))) : INT32_MAX;
+                // segmented minimum: owners are non-decreasing over the lanes, so
+                // each lane keeps the minimum of its owner's entries in this step
+                int segmin = val;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_down_sync(0xffffffffu, segmin, off);
+                    const int oy = __shfl_down_sync(0xffffffffu, o, off);
+                    if ((int)lane + off < 32 && oy == o) segmin = min(segmin, y);
+                }
+                // the first lane of each owner's run holds its minimum; hand it to the owner
+                const int op = __shfl_up_sync(0xffffffffu, o, 1);
+                const bool head = idx < total && (lane == 0 || op != o);
+                const unsigned hm = __ballot_sync(0xffffffffu, head);
+                // owner lane L takes the value of the head lane whose o == L (at most one per step)
+                for (unsigned h = hm; h; h &= h - 1) {
+                    const int hl = __ffs(h) - 1;
+                    const int ho = __shfl_sync(0xffffffffu, o, hl);
+                    const int hv = __shfl_sync(0xffffffffu, segmin, hl);
+                    if ((int)lane == ho) mine = min(mine, hv);
+                }
+            }
+            if (mine < ld) {  // units may lower labels concurrently: the atomic decides
+                const int old = atomicMin(p.label + d, mine);
+                if (mine < old) cc_mark(f_nxt, d, cnt);
             }
         }
-        if (mine < ld) {  // units may lower labels concurrently: the atomic decides
-            const int old = atomicMin(p.label + d, mine);
-            if (mine < old) cc_mark(f_nxt, d, cnt);
-        }
-    }
     }
 }
 
@@ -321,48 +321,48 @@ __global__ void __launch_bounds__(CC_T, 1) cc_kernel(ParamsCC p) {
         const long long per = (p.W + nwarps - 1) / nwarps;
         const long long iend = min((gwarp + 1) * per, (long long)p.W);
         for (long long i0 = gwarp * per; i0 < iend; i0 += 32) {
-        const long long il = i0 + (long long)lane;
-        const long long wl = il < iend ? cc_word(p, il) : -1;
-        const unsigned fwl = wl >= 0 ? __ldcg(f_cur + wl) : 0u;
-        if (fwl) f_cur[wl] = 0u;  // the buffer holds F_{i+2} next
-        for (unsigned todo = __ballot_sync(0xffffffffu, fwl != 0); todo; todo &= todo - 1) {  // warp-uniform
-            const int src = __ffs(todo) - 1;
-            const long long w = __shfl_sync(0xffffffffu, wl, src);
-            const unsigned fw = __shfl_sync(0xffffffffu, fwl, src);
-            const bool act = (fw >> lane) & 1u;
-            const int s = (int)(w * 32 + lane);
-            int beg = 0, deg = 0, ls = 0;
-            if (act) {
-                beg = __ldg(p.row_ptr + s);
-                deg = __ldg(p.row_ptr + s + 1) - beg;
-                ls = __ldcg(p.label + s);
-            }
-            const bool big = act && deg >= CC_CHUNK;
-            cc_emit_units(p, u_nxt, nxt, big, s, deg);
-            const int fdeg = (act && !big) ? deg : 0;
-            int incl = fdeg;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)lane >= o) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int excl = incl - fdeg;
-            for (int base = 0; base < total; base += 32) {
-                const int idx = base + (int)lane;
-                // owner: the last lane whose first entry is at or before idx
-                int o = 0;
-#pragma unroll
-                for (int st = 16; st > 0; st >>= 1) {
-                    const int ex = __shfl_sync(0xffffffffu, excl, (o + st) & 31);
-                    if (o + st < 32 && ex <= idx) o += st;
+            const long long il = i0 + (long long)lane;
+            const long long wl = il < iend ? cc_word(p, il) : -1;
+            const unsigned fwl = wl >= 0 ? __ldcg(f_cur + wl) : 0u;
+            if (fwl) f_cur[wl] = 0u;  // the buffer holds F_{i+2} next
+            for (unsigned todo = __ballot_sync(0xffffffffu, fwl != 0); todo; todo &= todo - 1) {  // warp-uniform
+                const int src = __ffs(todo) - 1;
+                const long long w = __shfl_sync(0xffffffffu, wl, src);
+                const unsigned fw = __shfl_sync(0xffffffffu, fwl, src);
+                const bool act = (fw >> lane) & 1u;
+                const int s = (int)(w * 32 + lane);
+                int beg = 0, deg = 0, ls = 0;
+                if (act) {
+                    beg = __ldg(p.row_ptr + s);
+                    deg = __ldg(p.row_ptr + s + 1) - beg;
+                    ls = __ldcg(p.label + s);
                 }
-                const int ob = __shfl_sync(0xffffffffu, beg, o);
-                const int oex = __shfl_sync(0xffffffffu, excl, o);
-                const int ol = __shfl_sync(0xffffffffu, ls, o);
-                if (idx < total) cc_relax(p, f_nxt, ol, __ldg(p.col + ob + (idx - oex)), cnt);
+                const bool big = act && deg >= CC_CHUNK;
+                cc_emit_units(p, u_nxt, nxt, big, s, deg);
+                const int fdeg = (act && !big) ? deg : 0;
+                int incl = fdeg;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int excl = incl - fdeg;
+                for (int base = 0; base < total; base += 32) {
+                    const int idx = base + (int)lane;
+                    // owner: the last lane whose first entry is at or before idx
+                    int o = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int ex = __shfl_sync(0xffffffffu, excl, (o + st) & 31);
+                        if (o + st < 32 && ex <= idx) o += st;
+                    }
+                    const int ob = __shfl_sync(0xffffffffu, beg, o);
+                    const int oex = __shfl_sync(0xffffffffu, excl, o);
+                    const int ol = __shfl_sync(0xffffffffu, ls, o);
+                    if (idx < total) cc_relax(p, f_nxt, ol, __ldg(p.col + ob + (idx - oex)), cnt);
+                }
             }
-        }
         }
 
         cc_count(nxt, cnt, s_red);
