@@ -38,7 +38,7 @@ NOMINAL_HBM_GBS = 8000.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat-s22-ef16")
@@ -173,19 +173,28 @@ class ClockSampler:
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi takes a moment to start: open the timed region only once it reports
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self) -> int:
+        """Index of the next sample: samples from here on were taken in the timed region."""
+        return len(self.samples)
 
     def _read(self):
         for line in self.proc.stdout:
             self.samples.append([x.strip() for x in line.split(",")])
 
-    def stop(self):
+    def stop(self, first: int = 0):
+        """Summary of the samples from index `first` on (the last one before it if none)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -197,7 +206,8 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for s in self.samples:
+        window = self.samples[first:] or self.samples[-1:]
+        for s in window:
             try:
                 sm.append(float(s[0]))
                 mx.append(float(s[1]))
@@ -463,6 +473,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    first_sample = clocks.mark()
     t_start.record(stream)
     for s in range(args.steps):
         plain_step(ev[s])
@@ -470,7 +481,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(first_sample)
     g.sync()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(args.steps) for j in range(k)]
