@@ -79,30 +79,6 @@ __device__ __forceinline__ void cc_relax(const ParamsCC& p, uint32_t* f_nxt, int
     }
 }
 
-// chunk units of the big rows of a warp's word: one atomic per warp
-__device__ __forceinline__ void cc_emit_units(const ParamsCC& p, int2* u_nxt, CountersCC* nxt, bool big, int s, int deg) {
-    const unsigned bm = __ballot_sync(0xffffffffu, big);
-    if (!bm) return;
-    const unsigned lane = lane_id();
-    const int nch = big ? (deg + CC_CHUNK - 1) / CC_CHUNK : 0;
-    int incl = nch;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&nxt->u_len, (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base + total > (unsigned long long)p.ucap) {
-        if (lane == 0) atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-        return;
-    }
-    const unsigned long long off = base + (incl - nch);
-    for (int k = 0; k < nch; ++k) u_nxt[off + k] = make_int2(s, k);
-}
-
 // Word of position i in the dealing order.  Warp k takes the contiguous
 // positions [k * per, (k + 1) * per).  The multiplicative scramble spreads
 // costly words over the warps: RMAT ids that share bit patterns have similar
@@ -250,25 +226,7 @@ __global__ void __launch_bounds__(CC_T, 1) cc_kernel(ParamsCC p) {
     for (long long v0 = gwarp * 32; v0 < p.n; v0 += nwarps * 32) {  // warp-uniform
         const long long v = v0 + lane;
         const int deg = v < p.n ? __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v) : 0;
-        const bool big = deg >= CC_CHUNK;
-        const unsigned bm = __ballot_sync(0xffffffffu, big);
-        if (!bm) continue;
-        const int nch = big ? (deg + CC_CHUNK - 1) / CC_CHUNK : 0;
-        int incl = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&ctl->n_big, (unsigned long long)total);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base + total <= (unsigned long long)p.ucap) {
-            for (int k = 0; k < nch; ++k) p.B[base + (incl - nch) + k] = make_int2((int)v, k);
-        } else if (lane == 0) {
-            atomicCAS(&ctl->bar.err, 0, (int)DEV_OVERFLOW);
-        }
+        append_units_warp(p.B, &ctl->n_big, p.ucap, &ctl->bar.err, deg >= CC_CHUNK, (int)v, deg, CC_CHUNK);
     }
     if (gtid == 0) ctl->slot[0].changed = (unsigned long long)p.n;  // F_0: dense, so iteration 0 pulls
     if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -338,7 +296,7 @@ __global__ void __launch_bounds__(CC_T, 1) cc_kernel(ParamsCC p) {
                     ls = __ldcg(p.label + s);
                 }
                 const bool big = act && deg >= CC_CHUNK;
-                cc_emit_units(p, u_nxt, nxt, big, s, deg);
+                append_units_warp(u_nxt, &nxt->u_len, p.ucap, &p.ctl->bar.err, big, s, deg, CC_CHUNK);
                 const int fdeg = (act && !big) ? deg : 0;
                 int incl = fdeg;
 #pragma unroll

@@ -203,6 +203,46 @@ __device__ __forceinline__ T warp_sum(T x) {
     return x;
 }
 
+// ------------------------------------------------------------ chunk units
+// A row of deg >= chunk entries is expanded as ceil(deg / chunk) units
+// (v, 0), (v, 1), ... appended to out[*len ...]; a list that would pass cap
+// records DEV_OVERFLOW in *err and drops the units.
+__device__ __forceinline__ void append_units(int2* out, unsigned long long* len, int64_t cap, int* err, int v, int deg,
+                                             int chunk) {
+    const int nch = (deg + chunk - 1) / chunk;
+    const unsigned long long ub = atomicAdd(len, (unsigned long long)nch);
+    if (ub + nch <= (unsigned long long)cap) {
+        for (int k = 0; k < nch; ++k) out[ub + k] = make_int2(v, k);
+    } else {
+        atomicCAS(err, 0, (int)DEV_OVERFLOW);
+    }
+}
+
+// The same for the lanes of a warp with big set: one atomic per warp.  Warp-uniform call.
+__device__ __forceinline__ void append_units_warp(int2* out, unsigned long long* len, int64_t cap, int* err, bool big,
+                                                  int v, int deg, int chunk) {
+    const unsigned bm = __ballot_sync(0xffffffffu, big);
+    if (!bm) return;
+    const unsigned lane = lane_id();
+    const int nch = big ? (deg + chunk - 1) / chunk : 0;
+    int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(len, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + total > (unsigned long long)cap) {
+        if (lane == 0) atomicCAS(err, 0, (int)DEV_OVERFLOW);
+        return;
+    }
+    const unsigned long long off = base + (incl - nch);
+    for (int k = 0; k < nch; ++k) out[off + k] = make_int2(v, k);
+}
+
 // ------------------------------------------------------------- launching
 int num_sms();
 int device_id();

@@ -215,38 +215,13 @@ __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
 }
 
 __device__ __forceinline__ void emit_units(const Params1& p, int2* u_out, Counters* c, int v, int deg) {
-    int nch = (deg + p.chunk - 1) / p.chunk;
-    unsigned long long ub = atomicAdd(&c->u_len, (unsigned long long)nch);
-    if (ub + nch <= (unsigned long long)p.ucap) {
-        for (int k = 0; k < nch; ++k) u_out[ub + k] = make_int2(v, k);
-    } else {
-        atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-    }
+    append_units(u_out, &c->u_len, p.ucap, &p.ctl->bar.err, v, deg, p.chunk);
 }
 
 // Chunk units of the big rows among a warp's claims: one atomic per warp.
 // Warp-uniform call.
 __device__ __forceinline__ void emit_units_warp(const Params1& p, int2* u_out, Counters* c, bool big, int v, int deg) {
-    const unsigned bm = __ballot_sync(0xffffffffu, big);
-    if (!bm) return;
-    const unsigned lane = lane_id();
-    int nch = big ? (deg + p.chunk - 1) / p.chunk : 0;
-    int incl = nch;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((int)lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&c->u_len, (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base + total > (unsigned long long)p.ucap) {
-        if (lane == 0) atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-        return;
-    }
-    const unsigned long long off = base + (incl - nch);
-    for (int k = 0; k < nch; ++k) u_out[off + k] = make_int2(v, k);
+    append_units_warp(u_out, &c->u_len, p.ucap, &p.ctl->bar.err, big, v, deg, p.chunk);
 }
 
 // Record vertices claimed in a push level: depth/parent, staged next-queue

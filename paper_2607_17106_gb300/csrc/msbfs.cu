@@ -196,13 +196,7 @@ __device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, in
 }
 
 __device__ __forceinline__ void ms_units(const ParamsMS& p, int2* u_out, CountersMS* c, int v, int deg) {
-    int nch = (deg + p.chunk - 1) / p.chunk;
-    unsigned long long ub = atomicAdd(&c->u_len, (unsigned long long)nch);
-    if (ub + nch <= (unsigned long long)p.ucap) {
-        for (int k = 0; k < nch; ++k) u_out[ub + k] = make_int2(v, k);
-    } else {
-        atomicCAS(&p.ctl->bar.err, 0, (int)DEV_OVERFLOW);
-    }
+    append_units(u_out, &c->u_len, p.ucap, &p.ctl->bar.err, v, deg, p.chunk);
 }
 
 __device__ __forceinline__ void ms_flush(MsLevel& L) {
