@@ -287,32 +287,65 @@ def cpu_baseline(n, src, dst, sources, budget_s=20.0, gpu_depth=None):
 
 
 # ------------------------------------------------------------ reference arm
+METRIC = "BFS GTEPS, plain single-source push/pull direction-optimising (batched+learned reported beside)"
+METRIC_MIXED = "BFS GTEPS, mixed batch of 256 queries over RMAT scales 16-22 in one persistent launch"
+
+
+def workload_desc(w, n: int, m: int) -> str:
+    return f"{w.name}: {describe(w)}, symmetrised+dedup, n={n}, m={m} directed"
+
+
+def mixed_queries():
+    """The mixed workload: RMAT graphs of scales 16..22 (edge factor 16, seed = scale),
+    256 queries whose graph is drawn uniformly (seed 106), sources seeded per graph."""
+    scales = list(range(16, 23))
+    graphs = [graphgen.rmat(sc, 16, seed=sc) for sc in scales]
+    goq = np.random.default_rng(106).integers(0, len(scales), 256).astype(np.int32)
+    srcs = np.zeros(256, np.int32)
+    for gi, (n, s, d) in enumerate(graphs):
+        idx = np.flatnonzero(goq == gi)
+        if len(idx):
+            srcs[idx] = graphgen.sample_sources(n, s, d, len(idx), 106 + gi)
+    return scales, graphs, goq, srcs
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return 0
-    w = graphgen.WORKLOADS[args.workload]
-    n, src, dst = w.edges()
-    sources = w.sources(n, src, dst)
     import oracle
-    adj = oracle.build_adjacency(n, src, dst)
-    deg = np.diff(adj.row_ptr)
+    if args.workload == MIXED:  # one query of the batch per step, in query order
+        scales, graphs, goq, srcs = mixed_queries()
+        adjs = {}
+        metric, wdesc = METRIC_MIXED, MIXED + ": 256 queries over RMAT scales 16..22; one query per step"
+    else:
+        w = graphgen.WORKLOADS[args.workload]
+        n, src, dst = w.edges()
+        sources = w.sources(n, src, dst)
+        adj = oracle.build_adjacency(n, src, dst)
+        metric, wdesc = METRIC, workload_desc(w, n, adj.m) + "; one of its seeded sources per step"
     times, edges = [], []
     for step in range(args.warmup + args.steps):
-        s = int(sources[step % len(sources)])
+        if args.workload == MIXED:
+            q = step % len(srcs)
+            gi = int(goq[q])
+            if gi not in adjs:
+                adjs[gi] = oracle.build_adjacency(*graphs[gi])
+            a, s = adjs[gi], int(srcs[q])
+        else:
+            a, s = adj, int(sources[step % len(sources)])
         t0 = time.perf_counter()
-        depth, _ = oracle.bfs(adj, s)
+        depth, _ = oracle.bfs(a, s)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-            edges.append(float(deg[depth >= 0].sum()) / 2.0)
+            edges.append(float(np.diff(a.row_ptr)[depth >= 0].sum()) / 2.0)
     value = sum(edges) / sum(times) / 1e9
-    line = {"impl": "reference", "metric": "BFS GTEPS (plain direction-optimising, per source)", "value": value,
+    line = {"impl": "reference", "metric": metric, "value": value,
             "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": w.name, "sources": "one seeded source per step",
-                       "engine": "CPU oracle (FIFO queue BFS), single thread"},
+            "config": {"workload": wdesc, "engine": "CPU oracle (FIFO queue BFS), single thread"},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} single-source searches"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -328,20 +361,9 @@ def run_mixed_bench(args, bg, torch, dist=None, rank=0, ws=1):
     """256 queries over RMAT graphs of scales 16..22 (edge factor 16, seeds 16..22),
     the graph of each query drawn uniformly (seed 106): one bfs_run_mixed launch
     against the same queries as per-graph 64-lane batches and one at a time."""
-    scales = list(range(16, 23))
-    graphs, edges_of = [], []
-    for sc in scales:
-        n, s, d = graphgen.rmat(sc, 16, seed=sc)
-        graphs.append((n, bg.Graph.build(n, s, d)))
-        edges_of.append((s, d))
-    q = 256
-    goq = np.random.default_rng(106).integers(0, len(scales), q).astype(np.int32)
-    srcs = np.zeros(q, np.int32)
-    for gi in range(len(scales)):
-        idx = np.flatnonzero(goq == gi)
-        if len(idx):
-            n, _ = graphs[gi]
-            srcs[idx] = graphgen.sample_sources(n, *edges_of[gi], len(idx), 106 + gi)
+    scales, edge_lists, goq, srcs = mixed_queries()
+    graphs = [(n, bg.Graph.build(n, s, d)) for n, s, d in edge_lists]
+    q = len(srcs)
     depth = [torch.empty(graphs[gi][0], dtype=torch.int32, device="cuda") for gi in goq]
     parent = [torch.empty(graphs[gi][0], dtype=torch.int32, device="cuda") for gi in goq]
     gl = [g for _, g in graphs]
@@ -391,7 +413,7 @@ def run_mixed_bench(args, bg, torch, dist=None, rank=0, ws=1):
     ms_single = e0.elapsed_time(e1)
     if rank != 0:
         return 0
-    line = {"metric": "BFS GTEPS, mixed batch of 256 queries over RMAT scales 16-22 in one persistent launch",
+    line = {"metric": METRIC_MIXED,
             "value": job_edges / (ms_mixed * 1e-3) / 1e9, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -628,12 +650,12 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "BFS GTEPS, plain single-source push/pull direction-optimising (batched+learned reported beside)",
+            "metric": METRIC,
             "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {describe(w)}, symmetrised+dedup, n={n}, m={info.m} directed; "
-                                   f"{k} seeded sources one at a time", "sources_per_step": k, "edges_per_step": edges,
+            "config": {"workload": workload_desc(w, n, info.m) + f"; {k} seeded sources one at a time",
+                       "sources_per_step": k, "edges_per_step": edges,
                        "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
                        "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=8 beta=48"},
             "roofline": roof, "per_search": teps_stats, "cpu_baseline": cpu, "e2e": e2e,
