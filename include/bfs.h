@@ -38,7 +38,8 @@ typedef enum {
     BFS_ENOMEM = 2,    /* device or host allocation failed */
     BFS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
     BFS_ETIMEOUT = 4,  /* a device-side wait (grid barrier) exceeded its limit; outputs undefined */
-    BFS_ERANGE = 5,    /* size beyond the int32 CSR limits (more than 2^31-1 directed entries) */
+    BFS_ERANGE = 5,    /* a limit was passed: more than 2^31-1 directed CSR entries, a search's
+                          max_levels, or the rows a statistics call may write */
     BFS_EVALIDATE = 6  /* internal consistency check failed (e.g. device error flag set) */
 } bfs_status;
 
