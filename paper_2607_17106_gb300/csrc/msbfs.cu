@@ -1039,6 +1039,7 @@ bfs_status run_msbfs(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* d
 bfs_status run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
                      const int32_t* sources, int32_t nq, int32_t* const* depth, int32_t* const* parent,
                      const bfs_options& o, cudaStream_t st) {
+    (void)n_graphs;  // bfs_run_mixed has checked every graph_of_query[q] against it
     std::map<int, std::vector<int>> by_graph;
     for (int q = 0; q < nq; ++q) by_graph[graph_of_query[q]].push_back(q);
     std::vector<MsUnit> units;
