@@ -59,6 +59,13 @@ def test_status_strings_and_argument_errors_need_no_gpu(lib):
     assert lib.bfs_run(None, None, 1, None, None, None, None) == bg.BFS_EINVAL
     with pytest.raises(bg.BfsError):
         bg._check(lib.bfs_run(None, None, 1, None, None, None, None))
+    # the reordering flag needs a symmetric build; the later entry points check their arguments
+    src = (ctypes.c_int32 * 2)(0, 1)
+    dst = (ctypes.c_int32 * 2)(1, 2)
+    assert lib.bfs_build_graph(3, 2, src, dst, bg.BFS_DEDUP | bg.BFS_REORDER_RCM, None, ctypes.byref(h)) == bg.BFS_EINVAL
+    assert b"BFS_SYMMETRIZE" in lib.bfs_last_error()
+    assert lib.bfs_components(None, None, None, None) == bg.BFS_EINVAL
+    assert lib.bfs_graph_permutation(None, None, None) == bg.BFS_EINVAL
 
 
 def test_library_has_no_oracle_dependency():
