@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-rcm", action="store_true", help="skip the Reverse Cuthill-McKee reordered leg")
     ap.add_argument("--profile-batched", type=int, default=0, metavar="R",
                     help="only run R 64-lane batched launches of the workload's sources and exit (for ncu)")
+    ap.add_argument("--levels", action="store_true",
+                    help="print a per-level time and byte breakdown of the single-source searches and exit")
     ap.add_argument("--policy-weights", default=os.path.join(ROOT, "paper_2607_17106_gb300", "policy_weights.npy"))
     return ap.parse_args()
 
@@ -93,18 +95,27 @@ def describe(w) -> str:
 
 
 # ------------------------------------------------------------ roofline model
-def bytes_model(stats: np.ndarray, n: int):
-    """Minimum DRAM bytes of one search from its per-level statistics.
+def level_bytes(stats: np.ndarray, n: int):
+    """Per-level minimum DRAM bytes of one search, push and pull form.
 
-    outputs: depth+parent written once per vertex (8n) and the visited bitmap
-    initialised once (n/8); per level the cheaper of
-      push: queue 4f + row offsets 8f + columns 4e_f + next queue 4d_new
-      pull: visited n/8 + row offsets 4u + scanned columns 4s_u + next bitmap n/8
+    From the per-level statistics f, e_f, u, s_u, d_new (Cascade 1; the pull
+    form of Section 5 reads s_u entries with early exit):
+      push: queue 4f + row offsets 8f + columns 4e_f + depth/parent writes
+            8d_new + next queue 4d_new + visited bitmap read and next bitmap
+            written once each n/4
+      pull: visited n/8 + row offsets 8u + scanned columns 4s_u + frontier
+            n/8 + depth/parent writes 8d_new + next bitmap n/8
     """
     f, e_f, u, s_u, d_new, e_u = (stats[:, i].astype(np.float64) for i in range(6))
-    push = 12 * f + 4 * e_f + 4 * d_new
-    pull = n / 8 + 4 * u + 4 * s_u + n / 8
-    return 8.0 * n + n / 8 + float(np.minimum(push, pull).sum())
+    push = 12 * f + 4 * e_f + 12 * d_new + n / 4
+    pull = 3 * n / 8 + 8 * u + 4 * s_u + 8 * d_new
+    return push, pull
+
+
+def bytes_model(stats: np.ndarray, n: int):
+    """B_min of one search: the cheaper form's bytes summed over its levels."""
+    push, pull = level_bytes(stats, n)
+    return float(np.minimum(push, pull).sum())
 
 
 def rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edges, plain_ms, batched_ms,
@@ -296,17 +307,7 @@ def workload_desc(w, n: int, m: int) -> str:
 
 
 def mixed_queries():
-    """The mixed workload: RMAT graphs of scales 16..22 (edge factor 16, seed = scale),
-    256 queries whose graph is drawn uniformly (seed 106), sources seeded per graph."""
-    scales = list(range(16, 23))
-    graphs = [graphgen.rmat(sc, 16, seed=sc) for sc in scales]
-    goq = np.random.default_rng(106).integers(0, len(scales), 256).astype(np.int32)
-    srcs = np.zeros(256, np.int32)
-    for gi, (n, s, d) in enumerate(graphs):
-        idx = np.flatnonzero(goq == gi)
-        if len(idx):
-            srcs[idx] = graphgen.sample_sources(n, s, d, len(idx), 106 + gi)
-    return scales, graphs, goq, srcs
+    return graphgen.mixed_batch()
 
 
 def run_reference(args):
@@ -426,6 +427,80 @@ def run_mixed_bench(args, bg, torch, dist=None, rank=0, ws=1):
     return 0
 
 
+# ------------------------------------------------------------ per-level breakdown
+DIR_NAMES = {0: "push-queue", 1: "push-bitmap", 2: "pull"}
+
+
+def level_breakdown(args, bg, torch, g, w, n, sources, opt):
+    """Per-level durations (device %globaltimer stamps of the level log) beside
+    each level's minimum bytes, push and pull, for the single-source searches.
+    Printed as markdown tables; levels are aggregated by index (short searches)
+    and by form and frontier size."""
+    k = len(sources)
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    cap = min(n + 2, 1 << 16)
+    log = (bg.bfs_level_record * cap)()
+    nlev = bg.ctypes.c_int32(0)
+    o = bg.options(**{f: getattr(opt, f) for f in ("batch", "mode", "policy", "alpha", "beta", "gamma", "chunk",
+                                                   "medium", "pull_serial", "block_threads")})
+    o.level_log = bg.ctypes.cast(log, bg.ctypes.POINTER(bg.bfs_level_record))
+    o.level_log_cap = cap
+    o.levels_out = bg.ctypes.pointer(nlev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    rows = []       # (level, dir, f, e_f, u, s_u, d_new, us, push_B, pull_B)
+    searches = []   # (levels, log µs, event µs)
+    for _ in range(max(1, args.warmup)):
+        g.run(np.array([sources[0]], np.int32), depth, parent, bg.options(batch=0))
+    torch.cuda.synchronize()
+    for j in range(k):
+        e0.record(stream)
+        g.run(np.array([sources[j]], np.int32), depth, parent, bg.options(batch=0))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ev_us = e0.elapsed_time(e1) * 1e3
+        g.run(np.array([sources[j]], np.int32), depth, parent, o)  # synchronises (level log)
+        L = nlev.value
+        st = g.level_stats(depth)
+        if L + 1 > cap or log[L].dir != -1 or len(st) != L:
+            raise RuntimeError(f"level log of source {j} incomplete ({L} levels, {len(st)} in the statistics)")
+        push, pull = level_bytes(st, n)
+        t = [log[i].t_ns for i in range(L + 1)]
+        for i in range(L):
+            rows.append((i, log[i].dir, *st[i, :5].tolist(), (t[i + 1] - t[i]) / 1e3, push[i], pull[i]))
+        searches.append((L, (t[L] - t[0]) / 1e3, ev_us))
+    R = np.array(rows, dtype=np.float64)
+    out = [f"## Per-level breakdown: {w.name}, {k} sources one at a time (block_threads {opt.block_threads})", "",
+           f"searches: mean {np.mean([x[0] for x in searches]):.1f} levels; mean time from the first level's "
+           f"start to the closing record {np.mean([x[1] for x in searches]):.1f} us; mean event-timed launch "
+           f"{np.mean([x[2] for x in searches]):.1f} us", ""]
+    bmin = np.minimum(R[:, 8], R[:, 9])
+    if int(R[:, 0].max()) < 40:
+        out += ["| level | searches | forms taken | mean f | mean e_f | mean u | mean s_u | mean d_new | mean us | "
+                "B_push MB | B_pull MB | B_min MB | GB/s at B_min |", "|" + "---|" * 13]
+        for lv in range(int(R[:, 0].max()) + 1):
+            sel = R[:, 0] == lv
+            dirs = ", ".join(f"{DIR_NAMES[d]} {int((R[sel, 1] == d).sum())}" for d in (0, 1, 2) if (R[sel, 1] == d).any())
+            us = R[sel, 7].mean()
+            out.append(f"| {lv} | {int(sel.sum())} | {dirs} | {R[sel, 2].mean():.0f} | {R[sel, 3].mean():.0f} | "
+                       f"{R[sel, 4].mean():.0f} | {R[sel, 5].mean():.0f} | {R[sel, 6].mean():.0f} | {us:.1f} | "
+                       f"{R[sel, 8].mean() / 1e6:.2f} | {R[sel, 9].mean() / 1e6:.2f} | {bmin[sel].mean() / 1e6:.2f} | "
+                       f"{bmin[sel].mean() / (us * 1e-6) / 1e9:.0f} |")
+        out.append("")
+    out += ["| form | frontier f | levels | total us (all searches) | mean us per level | B_min MB per level | "
+            "GB/s at B_min |", "|---|---|---|---|---|---|---|"]
+    lg = np.floor(np.log2(np.maximum(R[:, 2], 1)) / 4).astype(int)
+    for d in (0, 1, 2):
+        for b in sorted(set(lg[R[:, 1] == d].tolist())):
+            sel = (R[:, 1] == d) & (lg == b)
+            us = R[sel, 7].sum()
+            out.append(f"| {DIR_NAMES[d]} | [{16 ** b}, {16 ** (b + 1)}) | {int(sel.sum())} | {us:.0f} | "
+                       f"{us / sel.sum():.2f} | {bmin[sel].mean() / 1e6:.3f} | {bmin[sel].sum() / (us * 1e-6) / 1e9:.0f} |")
+    print("\n".join(out))
+    return 0
+
+
 # ------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -460,6 +535,8 @@ def main():
     depth = torch.empty((k, n), dtype=torch.int32, device="cuda")
     parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
     opt = bg.options(batch=0)
+    if args.levels:
+        return level_breakdown(args, bg, torch, g, w, n, sources, opt)
     if args.profile_batched > 0:
         for _ in range(args.profile_batched):
             g.run(sources, depth, parent, bg.options(batch=1))

@@ -192,3 +192,19 @@ WORKLOADS = {
                                  ns=64, ss=107),
     "ba-n22-m8": Workload("ba-n22-m8", "ba", dict(n=1 << 22, m=8), 8, 64, 108),
 }
+
+
+def mixed_batch(n_queries: int = 256, scales=tuple(range(16, 23)), seed: int = 106):
+    """The mixed multi-graph workload: RMAT graphs of the given scales (edge
+    factor 16, a=0.57 b=c=0.19, seed = scale) and n_queries queries whose graph
+    is drawn uniformly (numpy PCG64, `seed`), sources sampled per graph with
+    seed + graph index.  Returns (scales, [(n, src, dst)], graph_of_query, sources)."""
+    scales = list(scales)
+    graphs = [rmat(sc, 16, seed=sc) for sc in scales]
+    goq = np.random.default_rng(seed).integers(0, len(scales), n_queries).astype(np.int32)
+    srcs = np.zeros(n_queries, np.int32)
+    for gi, (n, s, d) in enumerate(graphs):
+        idx = np.flatnonzero(goq == gi)
+        if len(idx):
+            srcs[idx] = sample_sources(n, s, d, len(idx), seed + gi)
+    return scales, graphs, goq, srcs

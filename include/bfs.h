@@ -159,7 +159,10 @@ enum {
                                  the HEURISTIC elsewhere and when `mlp` is NULL */
 };
 
-/* One record per executed level, written when bfs_options.level_log != NULL. */
+/* One record per executed level, written when bfs_options.level_log != NULL.
+ * The single-source persistent and host-loop drives add, capacity allowing,
+ * a closing record after the last level (dir = -1, f = 0) whose t_ns marks
+ * the end of that level. */
 typedef struct {
     int32_t level;
     int32_t dir;          /* BFS_DIR_* used for this level */
@@ -250,7 +253,9 @@ bfs_status bfs_run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const
  * away.  For a directed graph it is an upper bound, and a pull level there
  * scans in-rows instead.  depth[n]: host or device
  * output of bfs_run for one source.  stats: host array of 6*max_levels int64.
- * *levels receives L.  Errors: EINVAL, ERANGE (L > max_levels).  Synchronises.
+ * *levels receives L.  Errors: EINVAL (null argument, max_levels <= 0, graph
+ * or depth on another device than the current one, a depth value outside
+ * [-1, n)), ERANGE (L > max_levels).  Synchronises.
  */
 bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
                            int32_t* levels, void* cuda_stream);
@@ -269,8 +274,10 @@ bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max
  * receives L.  The first call on a device looks up the scratch array's device
  * address, so make that first call before any stream capture.  Every call
  * shares the one array: calls that overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  Synchronises
- * `cuda_stream`.  Errors: EINVAL, ERANGE, ECUDA.
+ * host threads) race and must be serialised by the caller.  The table is
+ * computed as by bfs_level_stats, with the same caveat for directed graphs
+ * (s_u is then an upper bound).  Synchronises `cuda_stream`.  Errors: EINVAL
+ * (as bfs_level_stats, and depth in host memory), ERANGE, ECUDA.
  */
 bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
                                    int32_t* levels, void* cuda_stream);

@@ -141,6 +141,17 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         long long nunits = (long long)cv[1];
         long long e_f = (long long)cv[2];
         if (f == 0) {
+            // closing record: marks the end time of the last level
+            if (gtid == 0 && p.log && level < p.log_cap) {
+                bfs_level_record r;
+                r.level = level;
+                r.dir = -1;
+                r.f = 0;
+                r.e_f = 0;
+                r.m_u = m_u;
+                r.t_ns = (int64_t)globaltimer_ns();
+                p.log[level] = r;
+            }
             done = true;
             break;
         }
@@ -513,7 +524,7 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
     }
     if (o.levels_out) *o.levels_out = h.next_level;
     if (o.level_log && o.level_log_cap > 0) {
-        int nl = std::min(h.next_level, o.level_log_cap);
+        int nl = std::min(h.next_level + (h.done ? 1 : 0), o.level_log_cap);
         if (nl > 0) BFS_CUDA(cudaMemcpy(o.level_log, w->d_log, sizeof(bfs_level_record) * nl, cudaMemcpyDeviceToHost));
     }
     return BFS_OK;

@@ -49,6 +49,7 @@ struct CountersMS {
     unsigned long long e_f;    // degree sum of the appended vertices
     unsigned long long conv;   // cursor of a masks -> active-list conversion
     unsigned long long lanes;  // OR of the frontier masks: lanes that can still find vertices
+    unsigned long long done_e; // degree sum of the vertices that the level left seen by every live lane
 };
 
 struct CtlMS {
@@ -182,6 +183,7 @@ struct MsLevel {
     unsigned long long cnt;  // |{v : F_{i+1}[v] != 0}| (pull levels, this thread's share)
     uint64_t lanes;          // OR of the F_{i+1} masks this thread wrote
     uint64_t live;           // lanes with a non-empty frontier F_i
+    unsigned long long done_e;  // degree sum of vertices now seen by every live lane (this thread's share)
     int32_t* qbuf;
     int qn;                  // staged appends (warp-uniform)
 };
@@ -486,7 +488,10 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
             ((unsigned long long*)p.seen)[v] |= acc;
             L.lanes |= acc;
             L.cnt += 1;
-            L.ef += (unsigned long long)(g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
+            const unsigned long long dv =
+                (unsigned long long)(g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
+            L.ef += dv;
+            if (acc == miss) L.done_e += dv;  // no live lane misses v any more
         }
     }
 }
@@ -542,17 +547,18 @@ __device__ void ms_long_rows(const ParamsMS& p, const UnitView& g, MsSmem& sm, c
 // The deferred long rows found their lanes: depth, F_{i+1}, seen and the
 // level counters (after ms_long_rows, before the next level).
 __device__ void ms_long_finalize(const ParamsMS& p, const UnitView& g, MsSmem& sm, uint64_t* f_next, long long nl,
-                                 int dnext, CountersMS* nxt) {
+                                 int dnext, CountersMS* nxt, uint64_t live) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
-    unsigned long long cnt = 0, ef = 0;
+    unsigned long long cnt = 0, ef = 0, done = 0;
     uint64_t ln = 0;
     for (long long r = gtid; r < nl; r += gthreads) {
         const uint64_t acc = __ldcg(p.acc_long + r);
         if (!acc) continue;
         const int v = p.longv[r];
         ((unsigned long long*)f_next)[v] = acc;
-        ((unsigned long long*)p.seen)[v] |= acc;
+        const uint64_t old = ((const unsigned long long*)p.seen)[v];
+        ((unsigned long long*)p.seen)[v] = old | acc;
         uint64_t b = acc;
         while (b) {
             const int j = __ffsll((long long)b) - 1;
@@ -560,15 +566,19 @@ __device__ void ms_long_finalize(const ParamsMS& p, const UnitView& g, MsSmem& s
             b &= b - 1;
         }
         cnt += 1;
-        ef += (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
+        const unsigned long long dv = (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
+        ef += dv;
+        if (((old | acc) & live) == live) done += dv;
         ln |= acc;
     }
     cnt = warp_sum(cnt);
     ef = warp_sum(ef);
+    done = warp_sum(done);
     ln = warp_or64(ln);
     if ((threadIdx.x & 31) == 0) {
         if (cnt) atomicAdd(&nxt->a_len, cnt);
         if (ef) atomicAdd(&nxt->e_f, ef);
+        if (done) atomicAdd(&nxt->done_e, done);
         if (ln) atomicOr((unsigned long long*)&nxt->lanes, (unsigned long long)ln);
     }
 }
@@ -685,6 +695,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 ctl->slot[s].e_f = 0;
                 ctl->slot[s].conv = 0;
                 ctl->slot[s].lanes = 0;
+                ctl->slot[s].done_e = 0;
             }
             ctl->slot[0].lanes = g.lanes;
         }
@@ -711,9 +722,10 @@ __device__ void msbfs_body(const ParamsMS& p) {
         for (int level = 0;; ++level) {
             CountersMS* cur = &ctl->slot[level % 3];
             CountersMS* nxt = &ctl->slot[(level + 1) % 3];
-            const unsigned long long* const csrc[4] = {&cur->a_len, &cur->e_f, &cur->lanes, &cur->u_len};
-            unsigned long long cv[4];
-            cta_load_u64<4>(csrc, cv);
+            const unsigned long long* const csrc[5] = {&cur->a_len, &cur->e_f, &cur->lanes, &cur->u_len,
+                                                       &cur->done_e};
+            unsigned long long cv[5];
+            cta_load_u64<5>(csrc, cv);
             long long a = (long long)cv[0];
             long long e_f = (long long)cv[1];
             const uint64_t live = (uint64_t)cv[2];
@@ -722,7 +734,11 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 if (gtid == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
                 return;
             }
-            m_u = max(m_u - e_f, 1ll);
+            // m_u: degree sum of the vertices some live lane has not seen,
+            // the rows a pull level would scan (the batched reading of
+            // Beamer's unexplored edges; summing every lane's frontier edges
+            // instead drove it to zero within a few levels of a long search)
+            m_u = max(m_u - (long long)cv[4], 1ll);
             int dir = ms_decide(p, g, sm, level, a, e_f, m_u, a_prev, prev_dir, deg_max);
             if (ui == 0 && gtid == 0 && p.log && level < p.log_cap) {
                 bfs_level_record r;
@@ -755,6 +771,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 z->e_f = 0;
                 z->conv = 0;
                 z->lanes = 0;
+                z->done_e = 0;
             }
             MsLevel L;
             L.level = level;
@@ -766,12 +783,15 @@ __device__ void msbfs_body(const ParamsMS& p) {
             L.cnt = 0;
             L.lanes = 0;
             L.live = live;
+            L.done_e = 0;
             L.qbuf = sm.qbuf + warp * MS_QBUF;
             L.qn = 0;
             if (dir == BFS_DIR_PULL) ms_pull_level(p, g, L, sm, f_cur);
             else ms_push_level<T>(p, g, L, sm, a_cur, u_cur, f_cur, a, nunits);
             const uint64_t ln = warp_or64(L.lanes);
             if ((threadIdx.x & 31) == 0 && ln) atomicOr((unsigned long long*)&nxt->lanes, (unsigned long long)ln);
+            const unsigned long long dn = warp_sum(L.done_e);
+            if ((threadIdx.x & 31) == 0 && dn) atomicAdd(&nxt->done_e, dn);
             unsigned long long ef = warp_sum(L.ef);
             unsigned long long cn = warp_sum(L.cnt);
             if ((threadIdx.x & 31) == 0) sm.red[warp] = ef;
@@ -803,7 +823,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 if (nl > 0) {
                     ms_long_rows<T>(p, g, sm, f_cur, live, nl);
                     if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
-                    ms_long_finalize(p, g, sm, L.f_next, nl, level + 1, nxt);
+                    ms_long_finalize(p, g, sm, L.f_next, nl, level + 1, nxt, live);
                 }
             }
             if (gtid == 0) ctl->long_len = 0;
@@ -819,10 +839,17 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 unsigned long long av[1];
                 cta_load_u64<1>(asrc, av);
                 long long an = (long long)av[0];
+                unsigned long long done = 0;
                 for (long long q = gtid; q < an; q += gthreads) {
-                    int v = L.a_next[q];
-                    p.seen[v] |= ((const unsigned long long*)L.f_next)[v];
+                    const int v = L.a_next[q];
+                    const uint64_t old = p.seen[v];
+                    const uint64_t nw = old | ((const unsigned long long*)L.f_next)[v];
+                    p.seen[v] = nw;
+                    if ((nw & live) == live && (old & live) != live)
+                        done += (unsigned long long)(__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v));
                 }
+                done = warp_sum(done);
+                if ((threadIdx.x & 31) == 0 && done) atomicAdd(&nxt->done_e, done);
             }
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             a_prev = a;

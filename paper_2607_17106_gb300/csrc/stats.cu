@@ -20,10 +20,14 @@
 namespace bfsgb {
 namespace {
 
+// Largest depth of the search; a value outside [-1, n) (an uninitialised or
+// foreign buffer) makes the result INT32_MAX, which the host rejects.
 __global__ void max_depth_kernel(const int32_t* depth, int32_t n, int* out) {
     int mx = -1;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        mx = max(mx, depth[v]);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = depth[v];
+        mx = (d < -1 || d >= n) ? INT32_MAX : max(mx, d);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
@@ -82,6 +86,32 @@ __global__ void level_accum_kernel(const int32_t* row_ptr, const int32_t* col, c
     }
 }
 
+// Frees the call's stream-ordered scratch on every return path.
+struct AsyncFrees {
+    cudaStream_t st;
+    void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~AsyncFrees() {
+        for (void* q : p)
+            if (q) cudaFreeAsync(q, st);
+    }
+};
+
+// Checks shared by both statistics calls.
+bfs_status check_stats_args(const bfs_graph* g, const int32_t* depth, const int64_t* stats, int32_t max_levels) {
+    if (!g || !depth || !stats) return fail(BFS_EINVAL, "null argument");
+    if (max_levels <= 0) return fail(BFS_EINVAL, "max_levels must be positive");
+    if (device_id() != g->device)
+        return fail(BFS_EINVAL, "graph lives on device %d, current device is %d", g->device, device_id());
+    return BFS_OK;
+}
+
+bfs_status depth_levels(int h_max, int32_t n, int32_t max_levels, int* L) {
+    if (h_max >= n) return fail(BFS_EINVAL, "depth holds values outside [-1, %d)", n);
+    *L = h_max + 1;
+    if (*L > max_levels) return fail(BFS_ERANGE, "search has %d levels, max_levels = %d", *L, max_levels);
+    return BFS_OK;
+}
+
 }  // namespace
 }  // namespace bfsgb
 
@@ -89,38 +119,41 @@ using namespace bfsgb;
 
 extern "C" bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, int32_t max_levels, int64_t* stats,
                                       int32_t* levels, void* cuda_stream) {
-    if (!g || !depth || !stats || max_levels <= 0) return fail(BFS_EINVAL, "null argument or max_levels <= 0");
+    bfs_status rc = check_stats_args(g, depth, stats, max_levels);
+    if (rc != BFS_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    AsyncFrees scratch{st};
     const int32_t* d_depth = depth;
-    int32_t* tmp_depth = nullptr;
     if (!is_device_ptr(depth)) {
+        int32_t* tmp_depth = nullptr;
         BFS_CUDA(cudaMallocAsync(&tmp_depth, (size_t)g->n * 4, st));
+        scratch.p[0] = tmp_depth;
         BFS_CUDA(cudaMemcpyAsync(tmp_depth, depth, (size_t)g->n * 4, cudaMemcpyHostToDevice, st));
         d_depth = tmp_depth;
+    } else {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, depth) == cudaSuccess && a.type == cudaMemoryTypeDevice && a.device != g->device)
+            return fail(BFS_EINVAL, "depth lives on device %d, the graph on device %d", a.device, g->device);
     }
     int* d_max;
     BFS_CUDA(cudaMallocAsync(&d_max, 4, st));
+    scratch.p[1] = d_max;
     int h_max = -1;
     BFS_CUDA(cudaMemcpyAsync(d_max, &h_max, 4, cudaMemcpyHostToDevice, st));
     int blocks = num_sms() * 4;
     max_depth_kernel<<<blocks, 256, 0, st>>>(d_depth, g->n, d_max);
     BFS_CUDA(cudaMemcpyAsync(&h_max, d_max, 4, cudaMemcpyDeviceToHost, st));
     BFS_CUDA(cudaStreamSynchronize(st));
-    cudaFreeAsync(d_max, st);
-    int L = h_max + 1;
-    bfs_status rc = BFS_OK;
-    if (L > max_levels) {
-        if (tmp_depth) cudaFreeAsync(tmp_depth, st);
-        return fail(BFS_ERANGE, "search has %d levels, max_levels = %d", L, max_levels);
-    }
+    int L = 0;
+    rc = depth_levels(h_max, g->n, max_levels, &L);
+    if (rc != BFS_OK) return rc;
     if (levels) *levels = L;
-    if (L <= 0) {
-        if (tmp_depth) cudaFreeAsync(tmp_depth, st);
-        return BFS_OK;
-    }
+    if (L <= 0) return BFS_OK;
     unsigned long long *d_arr, *d_const;
     BFS_CUDA(cudaMallocAsync(&d_arr, (size_t)5 * L * 8, st));
+    scratch.p[2] = d_arr;
     BFS_CUDA(cudaMallocAsync(&d_const, 16, st));
+    scratch.p[3] = d_const;
     BFS_CUDA(cudaMemsetAsync(d_arr, 0, (size_t)5 * L * 8, st));
     BFS_CUDA(cudaMemsetAsync(d_const, 0, 16, st));
     size_t sm = (size_t)5 * L * 8;
@@ -129,13 +162,11 @@ extern "C" bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, 
     } else {
         level_accum_kernel<false><<<blocks, 256, 0, st>>>(g->row_ptr, g->col, d_depth, g->n, L, d_arr, d_const);
     }
+    BFS_CUDA(cudaGetLastError());
     std::vector<unsigned long long> arr((size_t)5 * L), cst(2);
     BFS_CUDA(cudaMemcpyAsync(arr.data(), d_arr, arr.size() * 8, cudaMemcpyDeviceToHost, st));
     BFS_CUDA(cudaMemcpyAsync(cst.data(), d_const, 16, cudaMemcpyDeviceToHost, st));
     BFS_CUDA(cudaStreamSynchronize(st));
-    cudaFreeAsync(d_arr, st);
-    cudaFreeAsync(d_const, st);
-    if (tmp_depth) cudaFreeAsync(tmp_depth, st);
     long long u = 0, eu = 0;
     for (int i = 0; i < L; ++i) {
         u += (long long)arr[2 * L + i];
@@ -148,7 +179,7 @@ extern "C" bfs_status bfs_level_stats(const bfs_graph* g, const int32_t* depth, 
         o[3] = o[5] - (long long)arr[4 * L + i];
         o[4] = (i + 1 < L) ? (int64_t)arr[0 * L + i + 1] : 0;
     }
-    return rc;
+    return BFS_OK;
 }
 
 // ------------------------------------------------------------ no-allocation variant
@@ -223,14 +254,19 @@ bfs_status noalloc_scratch(NoallocScratch** out) {
 
 extern "C" bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t* depth, int32_t max_levels,
                                               int64_t* stats, int32_t* levels, void* cuda_stream) {
-    if (!g || !depth || !stats || !levels) return fail(BFS_EINVAL, "null argument");
-    if (max_levels <= 0) return fail(BFS_EINVAL, "max_levels must be positive");
+    if (!levels) return fail(BFS_EINVAL, "null argument");
+    bfs_status rc = check_stats_args(g, depth, stats, max_levels);
+    if (rc != BFS_OK) return rc;
     if (max_levels > NOALLOC_MAX_LEVELS)
         return fail(BFS_ERANGE, "max_levels %d exceeds the fixed scratch limit of %d levels", max_levels,
                     NOALLOC_MAX_LEVELS);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, depth) != cudaSuccess) cudaGetLastError();
+    else if (a.type == cudaMemoryTypeDevice && a.device != g->device)
+        return fail(BFS_EINVAL, "depth lives on device %d, the graph on device %d", a.device, g->device);
     if (!is_device_ptr(depth)) return fail(BFS_EINVAL, "depth must be device memory");
     NoallocScratch* s = nullptr;
-    bfs_status rc = noalloc_scratch(&s);
+    rc = noalloc_scratch(&s);
     if (rc != BFS_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int blocks = num_sms() * 4;
@@ -239,8 +275,9 @@ extern "C" bfs_status bfs_level_stats_noalloc(const bfs_graph* g, const int32_t*
     int h_max = -1;
     BFS_CUDA(cudaMemcpyAsync(&h_max, &s->max_depth, 4, cudaMemcpyDeviceToHost, st));
     BFS_CUDA(cudaStreamSynchronize(st));
-    const int L = h_max + 1;
-    if (L > max_levels) return fail(BFS_ERANGE, "search has %d levels, max_levels = %d", L, max_levels);
+    int L = 0;
+    rc = depth_levels(h_max, g->n, max_levels, &L);
+    if (rc != BFS_OK) return rc;
     *levels = L;
     if (L <= 0) return BFS_OK;
     const size_t sm = (size_t)5 * L * 8;

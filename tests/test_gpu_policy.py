@@ -83,6 +83,40 @@ def test_gradient_and_adam_step_match_fp64_reference():
     assert np.max(np.abs(w - Pn)) <= 1e-6 + 1e-5 * lr
 
 
+@pytest.mark.parametrize("objective", ["ce", "regress"])
+def test_adam_trajectory_over_consecutive_steps(objective):
+    # six consecutive training calls on a changing batch: after every call the
+    # GPU's weights must follow the FP64 Adam trajectory (moments carried from
+    # call to call, bias correction at the call's step number) driven by the
+    # gradients the GPU reports; a kernel that dropped its moments between
+    # calls would move lr * sign(g) each step and fail from step 2 on
+    P0 = _params(25).astype(np.float32).astype(np.float64)
+    pol = bg.Policy(_identity_norm_weights(P0))
+    rng = np.random.default_rng(26)
+    rows, lr, steps = 1500, 1e-2, 6
+    Pref, m1, m2 = P0.copy(), np.zeros_like(P0), np.zeros_like(P0)
+    grad = torch.empty(bg.BFS_MLP_NPARAM, dtype=torch.float32, device="cuda")
+    for t in range(1, steps + 1):
+        X = rng.normal(0, 1, (rows, 10)).astype(np.float32)
+        Pgpu = pol.weights().astype(np.float64)[: bg.BFS_MLP_NPARAM]
+        if objective == "ce":
+            y = rng.integers(0, 3, rows).astype(np.int32)
+            _, g_ref = oracle.mlp_loss_grad(Pgpu, X.astype(np.float64), y)
+            pol.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), rows, lr, t, grad_out=grad)
+        else:
+            tg = -rng.exponential(1.0, (rows, 3)).astype(np.float32)
+            _, g_ref = oracle.mlp_regress_loss_grad(Pgpu, X.astype(np.float64), tg.astype(np.float64))
+            pol.train_step_regress(torch.from_numpy(X).cuda(), torch.from_numpy(tg).cuda(), rows, lr, t,
+                                   grad_out=grad)
+        torch.cuda.synchronize()
+        g = grad.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref)) <= 1e-4, t
+        oracle.adam_step(Pref, m1, m2, g, t=t, lr=lr, eps=1e-8)
+        w = pol.weights().astype(np.float64)[: bg.BFS_MLP_NPARAM]
+        # FP32 rounding of the weights and of each update, accumulated over t steps
+        assert np.max(np.abs(w - Pref)) <= t * (1e-6 + 1e-5 * lr), t
+
+
 def test_regression_gradient_and_adam_step_match_fp64_reference():
     P = _params(15).astype(np.float32).astype(np.float64)
     pol = bg.Policy(_identity_norm_weights(P))

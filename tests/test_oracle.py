@@ -5,7 +5,8 @@
 - invariants: edge depth gap <= 1, reached set == connected component (union-find)
 - validator: accepts oracle output, rejects each kind of corrupted parent/depth
 - per-level statistics: closed forms on path and complete graphs, identities of Cascade 1
-- MLP FP64 reference: central finite differences, zero-parameter closed form, Adam step 1
+- MLP FP64 reference: central finite differences, zero-parameter closed form; Adam at step 1, under a
+  constant gradient at every step, two steps by hand, momentum past a zero gradient
 - regression loss: finite differences, constant-output closed form, exact-fit zero
 """
 import itertools
@@ -320,6 +321,45 @@ def test_adam_first_step_is_lr_times_sign():
     g = np.array([0.3, -5.0, 1e-3])
     oracle.adam_step(P, m1, m2, g, t=1, lr=0.01, eps=1e-12)
     assert np.allclose(P, [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01], atol=1e-9)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    # Kingma & Ba, Algorithm 1: with the same gradient g at every step the
+    # bias-corrected moments are exactly g and g^2, so each step moves every
+    # parameter by lr * g / (|g| + eps), at t = 1 and at every later t
+    P0 = np.array([0.5, -1.5, 2.0, 0.0])
+    g = np.array([0.2, -3.0, 1e-2, 7.0])
+    P, m1, m2 = P0.copy(), np.zeros(4), np.zeros(4)
+    lr, eps = 0.003, 1e-8
+    for t in range(1, 11):
+        oracle.adam_step(P, m1, m2, g, t=t, lr=lr, eps=eps)
+        assert np.allclose(P, P0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-12), t
+
+
+def test_adam_two_steps_by_hand():
+    # beta1 = 1/2, beta2 = 3/4, g1 = 1, g2 = 3, eps = 0, lr = 1.
+    # step 1: m = 1/2, v = 1/4; corrections 1/2, 1/4 -> update 1 / sqrt(1) = 1
+    # step 2: m = 1/4 + 3/2 = 7/4, v = 3/16 + 9/4 = 39/16; corrections 3/4 and
+    #         7/16 -> m_hat = 7/3, v_hat = 39/7 -> update (7/3) / sqrt(39/7)
+    P, m1, m2 = np.array([10.0]), np.zeros(1), np.zeros(1)
+    oracle.adam_step(P, m1, m2, np.array([1.0]), t=1, lr=1.0, beta1=0.5, beta2=0.75, eps=0.0)
+    assert np.allclose(P, [9.0], atol=1e-14)
+    assert np.allclose([m1[0], m2[0]], [0.5, 0.25], atol=1e-15)
+    oracle.adam_step(P, m1, m2, np.array([3.0]), t=2, lr=1.0, beta1=0.5, beta2=0.75, eps=0.0)
+    assert np.allclose([m1[0], m2[0]], [7 / 4, 39 / 16], atol=1e-15)
+    assert np.allclose(P, [9.0 - (7 / 3) / np.sqrt(39 / 7)], atol=1e-14)
+
+
+def test_adam_momentum_carries_past_a_zero_gradient():
+    # default betas: a step with g = 1 then one with g = 0.  The first moment
+    # is then 0.9 * 0.1 = 0.09 over 1 - 0.81 = 0.19, i.e. 9/19, the second
+    # 0.999 * 0.001 over 1 - 0.999^2 = 0.001999, i.e. 999/1999: the parameter
+    # keeps moving although the gradient is zero
+    P, m1, m2 = np.array([0.0]), np.zeros(1), np.zeros(1)
+    lr = 0.01
+    oracle.adam_step(P, m1, m2, np.array([1.0]), t=1, lr=lr, eps=0.0)
+    oracle.adam_step(P, m1, m2, np.array([0.0]), t=2, lr=lr, eps=0.0)
+    assert np.allclose(P, [-lr - lr * (9 / 19) / np.sqrt(999 / 1999)], atol=1e-15)
 
 
 def test_directed_validation_follows_edge_direction():

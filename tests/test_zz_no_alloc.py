@@ -54,3 +54,64 @@ def test_no_alloc_level_stats_equal_the_allocating_call():
     assert rc == bg.BFS_ERANGE
     rc, _ = _noalloc(lib, gp, dp, 100)  # 3000 levels do not fit in 100
     assert rc == bg.BFS_ERANGE
+
+
+def _driver_pool():
+    """The device's default stream-ordered memory pool through the driver API
+    (the pool cudaMallocAsync draws from), or None where libcuda is absent."""
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError:
+        return None, None
+    dev = ctypes.c_int(0)
+    pool = ctypes.c_void_p()
+    if cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) != 0:
+        return None, None
+    if cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) != 0:
+        return None, None
+    return cu, pool
+
+
+def _pool_attr(cu, pool, attr):
+    v = ctypes.c_uint64(0)
+    assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+USED_CURRENT, USED_HIGH = 7, 8  # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
+
+
+def test_no_alloc_call_allocates_nothing():
+    # around two calls: the default pool's high-water mark (reset before the
+    # calls) stays at what was in use, device free memory is unchanged, and
+    # torch's allocator saw no allocation; the allocating call, between the
+    # same resets, does raise the mark (the probe is not blind)
+    lib = bg.load()
+    n, s, d = graphgen.rmat(14, 16, seed=5)
+    g = bg.Graph.build(n, s, d)
+    depth = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.run(graphgen.sample_sources(n, s, d, 1, seed=3), depth, None, bg.options(batch=0))
+    g.sync()
+    rc, ref = _noalloc(lib, g, depth, 64)  # first call on the device: symbol lookup
+    assert rc == bg.BFS_OK
+    cu, pool = _driver_pool()
+    if cu is None:
+        pytest.skip("driver API not loadable")
+    zero = ctypes.c_uint64(0)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    free0, _ = torch.cuda.mem_get_info()
+    used0 = _pool_attr(cu, pool, USED_CURRENT)
+    assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(zero)) == 0
+    for _ in range(2):
+        rc, got = _noalloc(lib, g, depth, 64)
+        assert rc == bg.BFS_OK and np.array_equal(got, ref)
+    torch.cuda.synchronize()
+    assert _pool_attr(cu, pool, USED_HIGH) <= used0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == before
+    # positive control: the allocating call draws scratch from that pool
+    assert cu.cuMemPoolSetAttribute(pool, USED_HIGH, ctypes.byref(zero)) == 0
+    assert np.array_equal(g.level_stats(depth, max_levels=64), ref)
+    assert _pool_attr(cu, pool, USED_HIGH) > used0
+    g.free()
