@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-rcm", action="store_true", help="skip the Reverse Cuthill-McKee reordered leg")
     ap.add_argument("--profile-batched", type=int, default=0, metavar="R",
                     help="only run R 64-lane batched launches of the workload's sources and exit (for ncu)")
+    ap.add_argument("--profile-single", type=int, default=0, metavar="R",
+                    help="only run the first R single-source searches of the workload and exit (for ncu)")
+    ap.add_argument("--mode", choices=["persistent", "host-loop", "graph"], default="persistent",
+                    help="drive of --profile-single: host-loop runs every level as its own launch")
     ap.add_argument("--levels", action="store_true",
                     help="print a per-level time and byte breakdown of the single-source searches and exit")
     ap.add_argument("--policy-weights", default=os.path.join(ROOT, "paper_2607_17106_gb300", "policy_weights.npy"))
@@ -537,6 +541,15 @@ def main():
     opt = bg.options(batch=0)
     if args.levels:
         return level_breakdown(args, bg, torch, g, w, n, sources, opt)
+    if args.profile_single > 0:
+        mode = {"persistent": bg.BFS_MODE_PERSISTENT, "host-loop": bg.BFS_MODE_HOST_LOOP,
+                "graph": bg.BFS_MODE_GRAPH}[args.mode]
+        for j in range(min(args.profile_single, k)):
+            g.run(sources[j:j + 1], depth[j], parent[j], bg.options(batch=0, mode=mode))
+        g.sync()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_single": args.profile_single, "mode": args.mode, "workload": w.name}))
+        return 0
     if args.profile_batched > 0:
         for _ in range(args.profile_batched):
             g.run(sources, depth, parent, bg.options(batch=1))
@@ -663,6 +676,13 @@ def main():
             pv[name] = {"gteps": edges / (vms * 1e-3) / 1e9, "ms_per_step": vms, "speedup_vs_fused": fms / vms,
                         "depth_equal_to_plain": same_depths()}
         extra["push_variants"] = pv
+        # frontier order of push-queue levels (Variants 6 and 7 against claim order)
+        fsv = {"claim_order_ms_per_step": fms}
+        for name, fs in (("device_sort", bg.BFS_SORT_DEVICE), ("tile_sort", bg.BFS_SORT_TILE)):
+            vms, _ = time_single(bg.options(batch=0, frontier_sort=fs))
+            fsv[name] = {"gteps": edges / (vms * 1e-3) / 1e9, "ms_per_step": vms, "speedup_vs_claim_order": fms / vms,
+                         "depth_equal_to_plain": same_depths()}
+        extra["frontier_sort"] = fsv
         gms, cnt = time_single(bg.options(batch=0, mode=bg.BFS_MODE_GRAPH), 8)
         pms, _ = time_single(bg.options(batch=0), 8)
         extra["graph_mode_single"] = {"sources": cnt, "ms_graph_mode": gms, "ms_persistent": pms,

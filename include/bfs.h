@@ -149,6 +149,18 @@ enum {
                                        the visited update happens in the filter pass */
 };
 
+/* Frontier order of push-queue levels (Section 7.2, Variants 6 and 7: the
+ * swizzle of F on its ranks, i.e. sorting the frontier).  Single-source
+ * persistent and host-loop drives; MS-BFS batches ignore it. */
+enum {
+    BFS_SORT_NONE = 0,   /* entries in the order they were claimed (default) */
+    BFS_SORT_DEVICE = 1, /* Variant 6: device-wide ascending vertex order before each push-queue level,
+                            built by a round trip through the frontier bitmap (F_i's vertices are distinct,
+                            so the bitmap is a counting sort of the queue) and an order-preserving compaction */
+    BFS_SORT_TILE = 2    /* Variant 7: each CTA sorts the frontier entries of its tile (bitonic sort in shared
+                            memory) before expanding them */
+};
+
 /* Per-level direction policy. */
 enum {
     BFS_POLICY_HEURISTIC = 0, /* Beamer: push->pull if e_f > m_u/alpha, pull->push if f < n/beta */
@@ -197,6 +209,7 @@ typedef struct {
     int32_t push_filter;     /* BFS_PUSH_* (BFS_PUSH_FUSED).  A filter form holds an edge frontier of up to
                                 m (target, source) pairs, 8 B each, allocated on first use; the CUDA-graph
                                 drive rejects it with EINVAL */
+    int32_t frontier_sort;   /* BFS_SORT_* (BFS_SORT_NONE); the CUDA-graph drive rejects a sort with EINVAL */
 } bfs_options;
 
 /* Fill `opt` with the defaults listed above. */

@@ -152,7 +152,7 @@ __global__ void g_decide(Params1 p, cudaGraphConditionalHandle h_while, cudaGrap
 // thousands of requests on one L2 sector (see cta_load_u64).
 struct GHead {
     int level, units_valid;
-    long long f, nunits, m_u;
+    long long f, nunits, m_u, e_f;
     int32_t* depth;
     int32_t* parent;
 };
@@ -166,6 +166,7 @@ __device__ __forceinline__ GHead cta_head(const Ctl1* ctl) {
         h.f = (long long)c->q_len;
         h.nunits = (long long)c->u_len;
         h.m_u = ctl->m_u;
+        h.e_f = (long long)c->e_f;
         h.units_valid = ctl->units_valid;
         h.depth = ctl->depth;
         h.parent = ctl->parent;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.qb = sm.t.qb + (threadIdx.x >> 5) * QBUF;
     L.qe = sm.t.qe + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
-    L.precheck = push_precheck(h.m_u, p.m);
+    L.precheck = push_precheck(h.m_u, p.m, h.e_f);
     const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const int2* u_cur = (level & 1) ? p.U1 : p.U0;
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     L.parent = h.parent;
     L.ef = 0;
     L.cnt = 0;
+    L.pairs_ok = pull_pairs_ok(h.e_f, h.m_u);
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     uint32_t* f_next = (level & 1) ? p.F0 : p.F1;
     pull_level<true>(p, L, f_cur, f_next, s_pull[threadIdx.x >> 5]);

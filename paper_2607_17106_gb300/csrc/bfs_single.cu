@@ -53,6 +53,7 @@ void free_ws1(Workspace1* w) {
         cudaFree(w->U[i]);
     }
     cudaFree(w->E);
+    cudaFree(w->cta_cnt);
     cudaFree(w->ctl);
     cudaFree(w->d_sticky);
     cudaFree(w->stage_depth);
@@ -65,13 +66,190 @@ void free_ws1(Workspace1* w) {
 }
 
 
+// ------------------------------------------------------------ small levels
+// Small-frontier mode.  A push-queue level whose frontier has at most
+// SMALL_F vertices and SMALL_EF edges is latency-bound: a grid-wide level
+// costs a grid barrier, a read of the global level counters and a global
+// append counter on top of its few memory round trips.  Such levels run on
+// CTA 0 alone, one after another, separated by __syncthreads: the next
+// level's counters live in shared memory, queue entries still go to the
+// global queues (so the grid can take over at any level), and P, depth and
+// parent are the global arrays.  The other CTAs wait on a generation word,
+// resetting their time limit whenever CTA 0 reports progress, and all CTAs
+// reload the loop state once CTA 0 publishes it.
+#ifndef BFS_SMALL_MODE
+#define BFS_SMALL_MODE 0
+#endif
+#ifndef BFS_SMALL_EF
+#define BFS_SMALL_EF 4096
+#endif
+#ifndef BFS_SMALL_F
+#define BFS_SMALL_F 2048
+#endif
+
+__device__ __forceinline__ bool small_level_fits(long long f, long long e_f) {
+    return e_f <= BFS_SMALL_EF && f <= BFS_SMALL_F;
+}
+
+// CTA 0: runs levels from `level` (already decided: push-queue, fits) while
+// they stay small push-queue levels; publishes the loop state and the next
+// level's counters, then the generation `gen`.  Block-uniform.
+template <int T>
+__device__ __noinline__ void small_levels(const Params1& p, TileSmem<T>& sm, int level, long long f, long long e_f, long long m_u,
+                             long long f_prev, int bm_valid, int level_end, unsigned gen, float* s_feat,
+                             float* s_mlp_out, const float* mlp_w) {
+    __shared__ Counters sc[2];
+    __shared__ int s_abort;
+    Ctl1* ctl = p.ctl;
+    const unsigned warp = threadIdx.x >> 5;
+    int prev_dir = BFS_DIR_PUSH_QUEUE;
+    bool done = false;
+    long long f_new = 0, ef_new = 0, u_new = 0;
+    for (int it = 0;; ++it) {
+        Counters* nx = &sc[level & 1];
+        if (threadIdx.x == 0) {
+            nx->q_len = 0;
+            nx->u_len = 0;
+            nx->e_f = 0;
+            if ((it & 63) == 0) s_abort = ld_volatile_i32(&ctl->bar.abort);
+        }
+        __syncthreads();
+        if (s_abort) return;  // a waiter gave up; it has raised the error
+        LevelCtx L;
+        L.level = level;
+        L.depth = p.depth;
+        L.parent = p.parent;
+        L.q_next = (level & 1) ? p.Q0 : p.Q1;
+        L.u_next = (level & 1) ? p.U0 : p.U1;
+        L.next = nx;  // shared memory: appends count with shared atomics
+        L.ef = 0;
+        L.cnt = 0;
+        L.qv = sm.t.qv + warp * QBUF;
+        L.qb = sm.t.qb + warp * QBUF;
+        L.qe = sm.t.qe + warp * QBUF;
+        L.qn = 0;
+        L.precheck = push_precheck(m_u, p.m, e_f);
+        L.pairs_ok = false;
+        const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
+        for (long long base = 0; base < f; base += T) {  // block-uniform
+            const long long q = base + threadIdx.x;
+            const int4 e = q < f ? __ldcg(q_cur + q) : make_int4(-1, 0, 0, 0);
+            push_tile<T>(p, L, sm, e.x, e.y, e.z, false);  // big rows too: their edges are few here
+        }
+        flush_qbuf(L);
+        const unsigned long long ef = warp_sum(L.ef);
+        if ((threadIdx.x & 31) == 0 && ef) atomicAdd(&nx->e_f, ef);
+        __syncthreads();
+        f_new = (long long)nx->q_len;
+        ef_new = (long long)nx->e_f;
+        u_new = (long long)nx->u_len;
+        if (threadIdx.x == 0) *(volatile int*)&ctl->small_beat = level;  // progress for the waiters
+        f_prev = f;
+        ++level;
+        if (f_new == 0) {
+            done = true;
+            if (threadIdx.x == 0 && p.log && level < p.log_cap) {
+                bfs_level_record r;
+                r.level = level;
+                r.dir = -1;
+                r.f = 0;
+                r.e_f = 0;
+                r.m_u = m_u;
+                r.t_ns = (int64_t)globaltimer_ns();
+                p.log[level] = r;
+            }
+            break;
+        }
+        if (level >= p.max_levels) {
+            if (threadIdx.x == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
+            done = true;
+            break;
+        }
+        const long long mu_next = m_u - ef_new;
+        const int dir = decide_dir(p, level, f_new, ef_new, mu_next, f_prev, prev_dir, s_feat, s_mlp_out, mlp_w);
+        if (dir != BFS_DIR_PUSH_QUEUE || !small_level_fits(f_new, ef_new) || level >= level_end) break;
+        m_u = mu_next;
+        if (threadIdx.x == 0 && p.log && level < p.log_cap) {
+            bfs_level_record r;
+            r.level = level;
+            r.dir = dir;
+            r.f = f_new;
+            r.e_f = ef_new;
+            r.m_u = m_u;
+            r.t_ns = (int64_t)globaltimer_ns();
+            p.log[level] = r;
+        }
+        f = f_new;
+        e_f = ef_new;
+    }
+    // hand the search back: the grid continues at `level`, whose queue was
+    // written to the global queue; m_u excludes that level's e_f, which the
+    // main loop subtracts itself
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) {
+            Counters* c = &ctl->slot[k];
+            const bool cur = k == level % 3;
+            c->q_len = cur ? (unsigned long long)f_new : 0ull;
+            c->u_len = cur ? (unsigned long long)u_new : 0ull;
+            c->e_f = cur ? (unsigned long long)ef_new : 0ull;
+            c->conv = 0;
+            c->e_len = 0;
+        }
+        ctl->next_level = level;
+        ctl->prev_dir = prev_dir;
+        ctl->bm_valid = bm_valid;
+        ctl->q_valid = level;
+        ctl->m_u = m_u;
+        ctl->f_prev = f_prev;
+        ctl->done = done ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_u32(&ctl->small_gen, gen);
+}
+
+// The other CTAs: wait until CTA 0 publishes generation `gen`.  The time
+// limit restarts whenever CTA 0 reports a new level, so a long run of small
+// levels is not mistaken for a hang.  Returns false when the wait was aborted.
+__device__ bool small_wait(Ctl1* ctl, unsigned gen, int64_t timeout_ns) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint64_t t0 = globaltimer_ns();
+        int beat = ld_volatile_i32(&ctl->small_beat);
+        while (ld_acquire_u32(&ctl->small_gen) != gen) {
+            __nanosleep(256);
+            const int b = ld_volatile_i32(&ctl->small_beat);
+            const uint64_t now = globaltimer_ns();
+            if (b != beat) {
+                beat = b;
+                t0 = now;
+            }
+            if (ld_volatile_i32(&ctl->bar.abort)) {
+                ok = 0;
+                break;
+            }
+            if ((int64_t)(now - t0) > timeout_ns) {
+                atomicCAS(&ctl->bar.err, 0, (int)DEV_TIMEOUT);
+                atomicExch(&ctl->bar.abort, 1);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ------------------------------------------------------------ the kernel
 // Dynamic shared memory of the persistent kernel: a copy of the policy
 // weights, evaluated by every CTA at every level when the policy is the MLP.
 constexpr size_t BFS1_DYN_SMEM = (size_t)NWEIGHTS * sizeof(float);
 extern __shared__ float bfs1_dyn_smem[];
 
-template <int T>
+// SORT: the frontier-sort variants are compiled in (a separate instantiation,
+// so that the default kernel carries none of their registers).
+template <int T, bool SORT>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
     __shared__ float s_feat[BFS_MLP_IN];
@@ -129,6 +307,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     bool done = __ldcg(&ctl->done) != 0;
     int level_end = level + p.level_count;
     const unsigned warp = threadIdx.x >> 5;
+    unsigned small_gen = 0;  // small-frontier hand-overs so far (the same on every CTA)
 
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
@@ -172,10 +351,34 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             r.t_ns = (int64_t)globaltimer_ns();
             p.log[level] = r;
         }
+#if BFS_SMALL_MODE
+        if (dir == BFS_DIR_PUSH_QUEUE && q_valid == level && level_end - level > 1 && small_level_fits(f, e_f) &&
+            p.push_filter == BFS_PUSH_FUSED && !(SORT && p.frontier_sort != BFS_SORT_NONE)) {
+            // CTA 0 runs this level and the small ones after it; the rest wait
+            ++small_gen;
+            if (blockIdx.x == 0) {
+                small_levels<T>(p, sm, level, f, e_f, m_u, f_prev, bm_valid, level_end, small_gen, s_feat, &s_mlp_out,
+                                mlp_w);
+                if (ld_volatile_i32(&ctl->bar.abort)) return;
+            } else if (!small_wait(ctl, small_gen, p.timeout_ns)) {
+                return;
+            }
+            level = __ldcg(&ctl->next_level);
+            prev_dir = __ldcg(&ctl->prev_dir);
+            bm_valid = __ldcg(&ctl->bm_valid);
+            q_valid = __ldcg(&ctl->q_valid);
+            m_u = __ldcg(&ctl->m_u);
+            f_prev = __ldcg(&ctl->f_prev);
+            done = __ldcg(&ctl->done) != 0;
+            continue;
+        }
+#endif
         int2* u_cur = (level & 1) ? p.U1 : p.U0;
         uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
         uint32_t* f_nxt = (level & 1) ? p.F0 : p.F1;
-        if (dir != BFS_DIR_PUSH_QUEUE && bm_valid != level) {
+        // Variant 6: a push-queue level expands F_i in ascending vertex order
+        const bool sort_dev = SORT && p.frontier_sort == BFS_SORT_DEVICE && dir == BFS_DIR_PUSH_QUEUE;
+        if ((dir != BFS_DIR_PUSH_QUEUE || sort_dev) && bm_valid != level) {
             // queue -> bitmap conversion of F_i
             for (long long w = gtid; w < p.W; w += gthreads) f_cur[w] = 0;
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -186,7 +389,19 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             bm_valid = level;
         }
-        if (dir == BFS_DIR_PUSH_QUEUE && q_valid != level) {
+        if (sort_dev) {
+            // ordered bitmap -> queue of F_i; chunk units only when no push
+            // level has made them (after pull levels)
+            sort_count<T>(p, sm, f_cur);
+            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            sort_emit<T>(p, sm, f_cur, q_cur, u_cur, cur, q_valid != level);
+            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            const unsigned long long* const usrc[1] = {&cur->u_len};
+            unsigned long long uv[1];
+            cta_load_u64<1>(usrc, uv);
+            nunits = (long long)uv[0];
+            q_valid = level;
+        } else if (dir == BFS_DIR_PUSH_QUEUE && q_valid != level) {
             // bitmap -> queue conversion of F_i (after pull levels)
             bitmap_to_queue<T>(p, sm, f_cur, q_cur, u_cur, cur);
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -217,11 +432,12 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.qb = sm.t.qb + warp * QBUF;
         L.qe = sm.t.qe + warp * QBUF;
         L.qn = 0;
-        L.precheck = push_precheck(m_u, p.m);
+        L.precheck = push_precheck(m_u, p.m, e_f);
+        L.pairs_ok = pull_pairs_ok(e_f, m_u);
         if (dir == BFS_DIR_PULL) {
-            pull_level<false>(p, L, f_cur, f_nxt, sm.pull[warp]);
+            pull_level_cta<false, T>(p, L, f_cur, f_nxt, sm.pull.w[warp], sm.pull.c);
         } else {
-            push_level<T>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
+            push_level<T, SORT>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
             if (p.push_filter != BFS_PUSH_FUSED) {
                 // the advance is complete everywhere before any pair is claimed
                 if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
@@ -231,33 +447,41 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
                 filter_level<T>(p, L, (long long)min(ev[0], (unsigned long long)p.ecap));
             }
         }
-        // e_f (and |F_{i+1}| for pull) of the next frontier: one atomic per CTA
-        unsigned long long ef = warp_sum(L.ef);
-        unsigned long long cn = warp_sum(L.cnt);
-        if ((threadIdx.x & 31) == 0) sm.red[warp] = ef;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0;
-            for (int i = 0; i < T / 32; ++i) t += sm.red[i];
-            if (t) atomicAdd(&nxt->e_f, t);
+        // e_f (and |F_{i+1}| for pull) of the next frontier: one atomic per
+        // CTA, issued by thread 0 after the barrier's own __syncthreads and
+        // before its arrival
+        const unsigned long long ef = warp_sum(L.ef);
+        const unsigned long long cn = warp_sum(L.cnt);
+        if ((threadIdx.x & 31) == 0) {
+            sm.red[warp] = ef;
+            sm.red2[warp] = cn;
         }
-        __syncthreads();
-        if (dir == BFS_DIR_PULL) {
-            if ((threadIdx.x & 31) == 0) sm.red[warp] = cn;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned long long t = 0;
-                for (int i = 0; i < T / 32; ++i) t += sm.red[i];
-                if (t) atomicAdd(&nxt->q_len, t);
-            }
-            bm_valid = level + 1;
-        } else {
-            q_valid = level + 1;
-        }
+        const bool pull_dir = dir == BFS_DIR_PULL;
+        if (pull_dir) bm_valid = level + 1;
+        else q_valid = level + 1;
         prev_dir = dir;
         f_prev = f;
+        const int done_level = level;
         ++level;
-        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+        const bool ok = grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns, [&]() {
+            unsigned long long te = 0, tc = 0;
+            for (int i = 0; i < T / 32; ++i) {
+                te += sm.red[i];
+                tc += sm.red2[i];
+            }
+            if (te) atomicAdd(&nxt->e_f, te);
+            if (pull_dir && tc) atomicAdd(&nxt->q_len, tc);
+#if BFS_LEVEL_PHASES
+            if (p.log && done_level < p.log_cap / 2)
+                atomicMax((unsigned long long*)&p.log[p.log_cap / 2 + done_level].t_ns, (unsigned long long)globaltimer_ns());
+#endif
+        });
+        if (!ok) return;
+#if BFS_LEVEL_PHASES
+        if (gtid == 0 && p.log && done_level < p.log_cap / 2) p.log[p.log_cap / 2 + done_level].m_u = (int64_t)globaltimer_ns();
+#else
+        (void)done_level;
+#endif
     }
     if (gtid == 0) {
         ctl->next_level = level;
@@ -273,9 +497,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
 
 // At most 40 registers a thread for T <= 512, so that 1536 threads (48 warps
 // of memory-level parallelism for the latency-bound gathers) fit on an SM.
-template <int T>
+template <int T, bool SORT>
 __global__ void __launch_bounds__(T, (1536 / T) > 0 ? (1536 / T) : 1) bfs1_kernel(Params1 p) {
-    bfs1_body<T>(p);
+    bfs1_body<T, SORT>(p);
     if (threadIdx.x == 0) {
         int e = ld_volatile_i32(&p.ctl->bar.err);
         if (e) atomicCAS(p.sticky, 0, e);
@@ -291,14 +515,19 @@ struct LaunchCfg {
 template <int T>
 cudaError_t launch_bfs1(const Params1& p, int blocks, cudaStream_t st) {
     void* args[] = {(void*)&p};
-    return cudaLaunchCooperativeKernel((const void*)bfs1_kernel<T>, dim3(blocks), dim3(T), args, BFS1_DYN_SMEM, st);
+    const void* k = p.frontier_sort != BFS_SORT_NONE ? (const void*)bfs1_kernel<T, true> : (const void*)bfs1_kernel<T, false>;
+    return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(T), args, BFS1_DYN_SMEM, st);
 }
 
 template <int T>
 int max_coop_blocks(int blocks_per_sm) {
     int per_sm = 0;
-    cudaFuncSetAttribute(bfs1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T>, T, BFS1_DYN_SMEM);
+    int per_sm_sorted = 0;
+    cudaFuncSetAttribute(bfs1_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
+    cudaFuncSetAttribute(bfs1_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T, false>, T, BFS1_DYN_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sorted, bfs1_kernel<T, true>, T, BFS1_DYN_SMEM);
+    per_sm = std::min(per_sm, per_sm_sorted);  // one grid size whichever instantiation runs
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     return per_sm * num_sms();
@@ -419,6 +648,14 @@ static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o,
     p.pull_serial = o.pull_serial;
     p.aggregate = o.claim_aggregate;
     p.push_filter = o.push_filter;
+    p.frontier_sort = o.frontier_sort;
+    if (o.frontier_sort == BFS_SORT_DEVICE) {
+        if (!w->cta_cnt && cudaMalloc(&w->cta_cnt, 4096 * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BFS_ENOMEM, "frontier sort counts");
+        }
+        p.cta_cnt = w->cta_cnt;
+    }
     if (o.push_filter != BFS_PUSH_FUSED) {
         // edge frontier: one level's advance appends at most m pairs
         if (w->ecap < g->m) {
@@ -456,6 +693,9 @@ static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o,
                 return fail(BFS_ENOMEM, "level log");
             w->log_cap = o.level_log_cap;
         }
+#if BFS_LEVEL_PHASES
+        BFS_CUDA(cudaMemsetAsync(w->d_log, 0, sizeof(bfs_level_record) * o.level_log_cap, st));
+#endif
         p.log = w->d_log;
         p.log_cap = o.level_log_cap;
     }
@@ -495,6 +735,8 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
     if (o.mode == BFS_MODE_GRAPH) return run_graph_mode(g, w, p, src_value, depth, parent, o, st);
     BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
     CoopLauncher launcher(o);
+    if (o.frontier_sort == BFS_SORT_DEVICE && launcher.blocks > 4096)
+        return fail(BFS_EINVAL, "frontier_sort supports at most 4096 CTAs (launch has %d)", launcher.blocks);
     auto launch = [&](const Params1& pp) -> cudaError_t { return launcher(pp, st); };
     if (o.mode == BFS_MODE_HOST_LOOP) {
         p.do_init = 1;
@@ -524,7 +766,11 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
     }
     if (o.levels_out) *o.levels_out = h.next_level;
     if (o.level_log && o.level_log_cap > 0) {
+#if BFS_LEVEL_PHASES
+        int nl = o.level_log_cap;  // the second half holds the phase times
+#else
         int nl = std::min(h.next_level + (h.done ? 1 : 0), o.level_log_cap);
+#endif
         if (nl > 0) BFS_CUDA(cudaMemcpy(o.level_log, w->d_log, sizeof(bfs_level_record) * nl, cudaMemcpyDeviceToHost));
     }
     return BFS_OK;

@@ -92,6 +92,7 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->blocks_per_sm = 0;
     o->claim_aggregate = 0;
     o->push_filter = BFS_PUSH_FUSED;
+    o->frontier_sort = BFS_SORT_NONE;
     o->barrier_timeout_ns = 2000000000ll;
     o->batch = 1;
 }
@@ -114,6 +115,10 @@ static bfs_status check_options(const bfs_options* in, bfs_options* o) {
         return fail(BFS_EINVAL, "bad push_filter %d", o->push_filter);
     if (o->push_filter != BFS_PUSH_FUSED && o->mode == BFS_MODE_GRAPH)
         return fail(BFS_EINVAL, "push_filter needs the persistent or host-loop drive");
+    if (o->frontier_sort < BFS_SORT_NONE || o->frontier_sort > BFS_SORT_TILE)
+        return fail(BFS_EINVAL, "bad frontier_sort %d", o->frontier_sort);
+    if (o->frontier_sort != BFS_SORT_NONE && o->mode == BFS_MODE_GRAPH)
+        return fail(BFS_EINVAL, "frontier_sort needs the persistent or host-loop drive");
     return BFS_OK;
 }
 

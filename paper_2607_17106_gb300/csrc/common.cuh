@@ -134,11 +134,19 @@ struct GridBarrier {
 // counter reaches the target, with a %globaltimer limit: on expiry it
 // records DEV_TIMEOUT, raises the abort flag and returns false, so every CTA
 // leaves its loop.  Returns false when the barrier was aborted.
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsigned& target, int64_t timeout_ns) {
+// `before_arrival` runs on thread 0 after the CTA's __syncthreads and before
+// the arrival, so its writes are published by the same release.
+struct NoArrivalWork {
+    __device__ void operator()() const {}
+};
+template <typename F = NoArrivalWork>
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsigned& target, int64_t timeout_ns,
+                                          F before_arrival = F()) {
     __shared__ int s_ok;
     __syncthreads();
     target += nblocks;
     if (threadIdx.x == 0) {
+        before_arrival();
         int ok = 1;
         // the release add publishes every write of this CTA made before the
         // __syncthreads above; the acquire load that sees the last arrival

@@ -35,6 +35,10 @@ struct Ctl1 {
     int32_t src;
     int32_t* depth;
     int32_t* parent;
+    // small-frontier mode: generation published by the CTA that ran the
+    // small levels, and its progress (the level it is on) for the waiters
+    unsigned small_gen;
+    int32_t small_beat;
 };
 
 struct Workspace1 {
@@ -47,6 +51,7 @@ struct Workspace1 {
     int4* Q[2] = {nullptr, nullptr};
     int2* U[2] = {nullptr, nullptr};
     int2* E = nullptr;  // push_filter: edge frontier, capacity ecap pairs (allocated on first use)
+    unsigned* cta_cnt = nullptr;  // frontier_sort: one count per CTA of the persistent launch
     int64_t ecap = 0;
     Ctl1* ctl = nullptr;
     int* d_sticky = nullptr;
@@ -101,6 +106,8 @@ struct Params1 {
     // tuning
     int32_t chunk, medium, pull_serial, aggregate;
     int32_t push_filter;  // BFS_PUSH_FUSED / _FILTER / _FILTER_PREDICATED
+    int32_t frontier_sort;  // BFS_SORT_*
+    unsigned* cta_cnt;    // BFS_SORT_DEVICE: frontier vertices of each CTA's word range
     int64_t timeout_ns;
     int32_t max_levels;
     bfs_level_record* log;
@@ -176,6 +183,9 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
 // rows make a few frontier words very hot, which the L1 then serves.
 
 // ------------------------------------------------------------ claiming
+#ifndef BFS_PREFETCH_CLAIM
+#define BFS_PREFETCH_CLAIM 0
+#endif
 constexpr int QBUF = 64;  // per-warp shared-memory staging of next-queue entries
 
 struct LevelCtx {
@@ -192,11 +202,30 @@ struct LevelCtx {
     int32_t* qe;
     int qn;                 // entries staged (warp-uniform)
     bool precheck;          // push: read P before the OR (most targets already visited)
+    bool pairs_ok;          // pull: dense blocks may take the two-words-at-a-time path
 };
 
+#ifndef BFS_PRECHECK_MIN_EF
+#define BFS_PRECHECK_MIN_EF 65536
+#endif
 // A push target is visited with probability about 1 - m_u / m (the explored
-// share of the edges); reading P before the OR pays once most are.
-__device__ __forceinline__ bool push_precheck(long long m_u, long long m) { return 2 * m_u < m; }
+// share of the edges); reading P before the OR pays once most are and the
+// level has enough candidates for the ORs' throughput to matter (on a small
+// level the extra read only lengthens the chain).
+__device__ __forceinline__ bool push_precheck(long long m_u, long long m, long long e_f) {
+    return 2 * m_u < m && e_f >= BFS_PRECHECK_MIN_EF;
+}
+
+#ifndef BFS_PULL_PAIRS_RATIO
+#define BFS_PULL_PAIRS_RATIO 0.0f
+#endif
+// Pull: the two-words-at-a-time path of dense blocks costs, per pair of
+// words, the longest scan among its 64 vertices, so it pays only when nearly
+// every unvisited vertex finds a frontier neighbour at once -- when the
+// frontier's edges e_f are large against the unexplored edges m_u.
+__device__ __forceinline__ bool pull_pairs_ok(long long e_f, long long m_u) {
+    return (float)e_f >= BFS_PULL_PAIRS_RATIO * (float)m_u;
+}
 
 // Move the warp's staged queue entries to the next queue: one atomic per
 // flush instead of one per claiming round.  An entry carries its vertex's row
@@ -241,6 +270,11 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
         L.depth[v] = L.level + 1;
         if (L.parent) L.parent[v] = u;
         L.ef += (unsigned long long)deg;
+#if BFS_PREFETCH_CLAIM
+        // the next push level reads this row: start bringing its first
+        // sector into L2 now, off the next level's dependent chain
+        if (deg > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.col + rb));
+#endif
     }
     L.qn += c;
     emit_units_warp(p, L.u_next, L.next, claimed && deg >= p.chunk, v, deg);
@@ -356,6 +390,15 @@ struct PullWarpSmem {
     int nl;
 };
 
+// The open words of a round's dense pull blocks, shared by the CTA's warps.
+template <int T>
+struct PullCtaSmem {
+    int n;         // words in the list
+    int next;      // cursor of the warps draining it
+    int word[T];   // word index of P
+    unsigned pw[T];  // its P word
+};
+
 // Shared memory of a CTA running level kernels.  Push levels use the tile
 // scratch and the warps' next-queue staging; pull levels use the per-warp
 // pull scratch; no level uses both, so they share storage.
@@ -371,10 +414,14 @@ struct TileSmem {
             int32_t qb[(T / 32) * QBUF];
             int32_t qe[(T / 32) * QBUF];
         } t;
-        PullWarpSmem pull[T / 32];
+        struct {
+            PullWarpSmem w[T / 32];
+            PullCtaSmem<T> c;
+        } pull;
     };
     int scan_tmp[33];
     unsigned long long red[T / 32];
+    unsigned long long red2[T / 32];
     unsigned long long base;
 };
 
@@ -455,20 +502,62 @@ __device__ __forceinline__ void push_unit(const Params1& p, LevelCtx& L, int2 un
     }
 }
 
+// Variant 7 (BFS_SORT_TILE): the CTA's tile of frontier entries -- entries of
+// threads 0 .. cnt-1 are valid -- sorted by vertex in shared memory with a
+// bitonic network over the next power of two >= cnt.  Block-uniform.
+template <int T>
+__device__ __forceinline__ void tile_sort(TileSmem<T>& sm, int4& e, int cnt) {
+    int p2 = 1;
+    while (p2 < cnt) p2 <<= 1;
+    const int t = (int)threadIdx.x;
+    __syncthreads();  // a previous tile's readers of sm.t are done
+    if (t < p2) {
+        sm.t.src[t] = t < cnt ? e.x : INT32_MAX;
+        sm.t.beg[t] = e.y;
+        sm.t.lim[t] = e.z;
+    }
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int o = t ^ j;
+            if (t < p2 && o > t) {
+                const bool up = (t & k) == 0;
+                const int a = sm.t.src[t], b = sm.t.src[o];
+                if ((a > b) == up) {
+                    sm.t.src[t] = b;
+                    sm.t.src[o] = a;
+                    const int by = sm.t.beg[t], bz = sm.t.lim[t];
+                    sm.t.beg[t] = sm.t.beg[o];
+                    sm.t.lim[t] = sm.t.lim[o];
+                    sm.t.beg[o] = by;
+                    sm.t.lim[o] = bz;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (t < cnt) e = make_int4(sm.t.src[t], sm.t.beg[t], sm.t.lim[t], 0);
+    __syncthreads();  // push_tile reuses sm.t
+}
+
 // Push level.  Queue levels deal the frontier in passes of gridDim * T
 // entries: thread t of CTA b takes entry pass * gridDim * T + b + gridDim * t,
 // so a small frontier spreads over one thread of many CTAs.  Each entry carries
 // its row bounds.  Bitmap levels deal tiles of T/32 words of F_i round-robin.
 // Then the chunk units of F_i's big rows, round robin (their rows are skipped
 // in the tiles).
-template <int T>
+template <int T, bool SORT = false>
 __device__ void push_level(const Params1& p, LevelCtx& L, TileSmem<T>& sm, int dir, const int4* q_cur,
                            const int2* u_cur, const uint32_t* f_cur, long long f, long long nunits, bool units_valid) {
     const long long G = gridDim.x;
     if (dir == BFS_DIR_PUSH_QUEUE) {
         for (long long base = 0; base + blockIdx.x < f; base += G * T) {  // CTA-uniform
             const long long q = base + blockIdx.x + G * threadIdx.x;
-            const int4 e = q < f ? __ldcg(q_cur + q) : make_int4(-1, 0, 0, 0);
+            int4 e = q < f ? __ldcg(q_cur + q) : make_int4(-1, 0, 0, 0);
+            if (SORT && p.frontier_sort == BFS_SORT_TILE) {
+                const long long cnt = (f - base - blockIdx.x + G - 1) / G;  // entries of this tile
+                tile_sort<T>(sm, e, (int)min(cnt, (long long)T));
+            }
             push_tile<T>(p, L, sm, e.x, e.y, e.z, units_valid);
         }
     } else {
@@ -524,132 +613,153 @@ constexpr int PULL_SERIAL_MAX = 32;  // row entries one lane scans before its wa
 // in-neighbours a lane loads and tests per serial step: the loads of one step
 // are independent, so a step costs about one memory round trip whatever R is
 constexpr int PULL_R = BFS_PULL_R;
+#ifndef BFS_PULL_LONG_U
+#define BFS_PULL_LONG_U 1
+#endif
+// 32-entry groups a warp loads per step when it finishes a deferred long row
+constexpr int PULL_LONG_U = BFS_PULL_LONG_U;
 
 template <bool NC>
 __device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
     return NC ? __ldg(a + i) : a[i];
 }
 
-// Dense block of a pull level: the warp finishes the block's words two at a
-// time, lane = vertex.  An unvisited lane scans its in-neighbours in ascending
-// order and stops at the first one in F_i (ANY = the lowest-index frontier
-// neighbour); rows longer than `pull_serial` entries are finished by the
-// whole warp 32 entries at a time.  The warp writes the words of P and of
-// F_{i+1} with plain stores (it owns them).  Warp-uniform.
+#ifndef BFS_PULL_WPI
+#define BFS_PULL_WPI 2
+#endif
+constexpr int PULL_WPI = BFS_PULL_WPI;  // words a dense pull block finishes per iteration
+
+// Dense words of a pull level, PULL_WPI at a time, lane = vertex: wv[k] is a
+// word index of P (-1 for none) and pw[k] its P word.  An unvisited lane
+// scans its in-neighbours in ascending order and stops at the first one in
+// F_i (ANY = the lowest-index frontier neighbour); rows longer than
+// `pull_serial` entries are finished by the whole warp, 4 x 32 entries a step.
+// The warp writes the words of P and of F_{i+1} with plain stores (it owns
+// them).  Warp-uniform.
+template <bool NC>
+__device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                           const long long (&wv)[PULL_WPI], const unsigned (&pw)[PULL_WPI]) {
+    const unsigned lane = lane_id();
+    const int dnext = L.level + 1;
+    const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
+    bool unvis[PULL_WPI], found[PULL_WPI];
+    int beg[PULL_WPI], end[PULL_WPI], j[PULL_WPI], par[PULL_WPI];
+#pragma unroll
+    for (int k = 0; k < PULL_WPI; ++k) {
+        unvis[k] = !((pw[k] >> lane) & 1u);
+        const long long v = wv[k] * 32 + lane;
+        beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
+        end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
+        j[k] = beg[k];
+        found[k] = false;
+        par[k] = -1;
+    }
+    // ascending scans of the rows advance together, PULL_R entries a step;
+    // the first frontier entry in row order is the parent
+    for (int step = 0; step < serial; step += PULL_R) {
+        int u[PULL_WPI][PULL_R];
+        unsigned fw[PULL_WPI][PULL_R];
+        bool live = false;
+#pragma unroll
+        for (int k = 0; k < PULL_WPI; ++k) {
+            const bool lk = !found[k] && j[k] < end[k];
+#pragma unroll
+            for (int r = 0; r < PULL_R; ++r)
+                u[k][r] = (lk && j[k] + r < end[k]) ? __ldg(p.csc_col + j[k] + r) : -1;
+            live |= lk;
+        }
+        if (!live) break;
+#pragma unroll
+        for (int k = 0; k < PULL_WPI; ++k)
+#pragma unroll
+            for (int r = 0; r < PULL_R; ++r) fw[k][r] = u[k][r] >= 0 ? ld_word<NC>(f_cur, u[k][r] >> 5) : 0u;
+#pragma unroll
+        for (int k = 0; k < PULL_WPI; ++k) {
+            if (u[k][0] < 0) continue;
+            int adv = PULL_R;
+#pragma unroll
+            for (int r = PULL_R - 1; r >= 0; --r)
+                if (u[k][r] >= 0 && ((fw[k][r] >> (u[k][r] & 31)) & 1u)) adv = r;
+            if (adv < PULL_R) {
+                found[k] = true;
+                par[k] = u[k][adv];
+                j[k] += adv;
+            } else {
+                j[k] += PULL_R;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PULL_WPI; ++k) {
+        if (wv[k] < 0) break;  // warp-uniform
+        unsigned rm = __ballot_sync(0xffffffffu, unvis[k] && !found[k] && j[k] < end[k]);
+        while (rm) {
+            const int l = __ffs(rm) - 1;
+            const int bl = __shfl_sync(0xffffffffu, j[k], l);
+            const int el = __shfl_sync(0xffffffffu, end[k], l);
+            // 4 x 32 entries a step, all column loads issued before the
+            // frontier tests; the first hit in row order is the parent
+            int hit = -1;
+            for (int base = bl; base < el && hit < 0; base += 128) {
+                int uu[4];
+                unsigned fw[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int idx = base + q * 32 + (int)lane;
+                    uu[q] = idx < el ? __ldg(p.csc_col + idx) : -1;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned hb = __ballot_sync(0xffffffffu, uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u));
+                    if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[q], __ffs(hb) - 1);
+                }
+            }
+            if ((int)lane == l && hit >= 0) {
+                found[k] = true;
+                par[k] = hit;
+            }
+            rm &= rm - 1;
+        }
+        const long long w = wv[k];
+        const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
+        if (lane == 0) {
+            f_next[w] = nb;
+            if (nb) p.P[w] = pw[k] | nb;
+        }
+        if (found[k]) {
+            const long long v = w * 32 + lane;
+            L.depth[v] = dnext;
+            if (L.parent) L.parent[v] = par[k];
+            L.ef += (unsigned long long)(p.symmetric ? (end[k] - beg[k])
+                                                     : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+            L.cnt += 1;
+        }
+    }
+}
+
+// Dense block of a pull level (32 words, the block's word l in lane l): the
+// warp finishes its words PULL_WPI at a time.  Warp-uniform.
 template <bool NC>
 __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
                                                  uint32_t* f_next, long long bi, long long S, unsigned pwl) {
     const unsigned lane = lane_id();
-    const int dnext = L.level + 1;
-    const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
     const long long wl = bi + lane * S;
     if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
     unsigned todo = __ballot_sync(0xffffffffu, pwl != 0xffffffffu);
     while (todo) {
-        int wi[2];
-        unsigned pw[2];
+        long long wv[PULL_WPI];
+        unsigned pw[PULL_WPI];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            wi[k] = todo ? __ffs(todo) - 1 : -1;
+        for (int k = 0; k < PULL_WPI; ++k) {
+            const int wi = todo ? __ffs(todo) - 1 : -1;
             if (todo) todo &= todo - 1;
-            pw[k] = __shfl_sync(0xffffffffu, pwl, wi[k] < 0 ? 0 : wi[k]);
-            if (wi[k] < 0) pw[k] = 0xffffffffu;
+            pw[k] = __shfl_sync(0xffffffffu, pwl, wi < 0 ? 0 : wi);
+            if (wi < 0) pw[k] = 0xffffffffu;
+            wv[k] = wi < 0 ? -1 : bi + wi * S;
         }
-        bool unvis[2], found[2];
-        int beg[2], end[2], j[2], par[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            unvis[k] = !((pw[k] >> lane) & 1u);
-            const long long v = (bi + wi[k] * S) * 32 + lane;
-            beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
-            end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
-            j[k] = beg[k];
-            found[k] = false;
-            par[k] = -1;
-        }
-        // ascending scans of both rows advance together, PULL_R entries a step;
-        // the first frontier entry in row order is the parent
-        for (int step = 0; step < serial; step += PULL_R) {
-            int u[2][PULL_R];
-            unsigned fw[2][PULL_R];
-            bool live = false;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const bool lk = !found[k] && j[k] < end[k];
-#pragma unroll
-                for (int r = 0; r < PULL_R; ++r)
-                    u[k][r] = (lk && j[k] + r < end[k]) ? __ldg(p.csc_col + j[k] + r) : -1;
-                live |= lk;
-            }
-            if (!live) break;
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
-                for (int r = 0; r < PULL_R; ++r) fw[k][r] = u[k][r] >= 0 ? ld_word<NC>(f_cur, u[k][r] >> 5) : 0u;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (u[k][0] < 0) continue;
-                int adv = PULL_R;
-#pragma unroll
-                for (int r = PULL_R - 1; r >= 0; --r)
-                    if (u[k][r] >= 0 && ((fw[k][r] >> (u[k][r] & 31)) & 1u)) adv = r;
-                if (adv < PULL_R) {
-                    found[k] = true;
-                    par[k] = u[k][adv];
-                    j[k] += adv;
-                } else {
-                    j[k] += PULL_R;
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (wi[k] < 0) break;  // warp-uniform
-            unsigned rm = __ballot_sync(0xffffffffu, unvis[k] && !found[k] && j[k] < end[k]);
-            while (rm) {
-                const int l = __ffs(rm) - 1;
-                const int bl = __shfl_sync(0xffffffffu, j[k], l);
-                const int el = __shfl_sync(0xffffffffu, end[k], l);
-                // 4 x 32 entries a step, all column loads issued before the
-                // frontier tests; the first hit in row order is the parent
-                int hit = -1;
-                for (int base = bl; base < el && hit < 0; base += 128) {
-                    int uu[4];
-                    unsigned fw[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int idx = base + q * 32 + (int)lane;
-                        uu[q] = idx < el ? __ldg(p.csc_col + idx) : -1;
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const unsigned hb = __ballot_sync(0xffffffffu, uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u));
-                        if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[q], __ffs(hb) - 1);
-                    }
-                }
-                if ((int)lane == l && hit >= 0) {
-                    found[k] = true;
-                    par[k] = hit;
-                }
-                rm &= rm - 1;
-            }
-            const long long w = bi + wi[k] * S;
-            const unsigned nb = __ballot_sync(0xffffffffu, found[k]);
-            if (lane == 0) {
-                f_next[w] = nb;
-                if (nb) p.P[w] = pw[k] | nb;
-            }
-            if (found[k]) {
-                const long long v = w * 32 + lane;
-                L.depth[v] = dnext;
-                if (L.parent) L.parent[v] = par[k];
-                L.ef += (unsigned long long)(p.symmetric ? (end[k] - beg[k])
-                                                         : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
-                L.cnt += 1;
-            }
-        }
+        pull_words<NC>(p, L, f_cur, f_next, wv, pw);
     }
 }
 
@@ -704,29 +814,40 @@ __device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, Pu
     const unsigned lane = lane_id();
     for (int r = 0; r < nl; ++r) {
         const int v = ws.lv[r], jl = ws.lj[r], el = ws.le[r], bl = ws.lb[r];
-        for (int base = jl; base < el; base += 32) {
-            const int idx = base + (int)lane;
-            int uu = 0;
-            bool h = false;
-            if (idx < el) {
-                uu = __ldg(p.csc_col + idx);
-                h = (ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u;
+        // PULL_LONG_U x 32 entries a step: every column load, then every
+        // frontier test, then the first hit in row order
+        int hit = -1;
+        for (int base = jl; base < el && hit < 0; base += 32 * PULL_LONG_U) {
+            int uu[PULL_LONG_U];
+            unsigned fw[PULL_LONG_U];
+#pragma unroll
+            for (int q = 0; q < PULL_LONG_U; ++q) {
+                const int idx = base + q * 32 + (int)lane;
+                uu[q] = idx < el ? __ldg(p.csc_col + idx) : -1;
             }
-            const unsigned hb = __ballot_sync(0xffffffffu, h);
-            if (hb) {
-                const int hit = __shfl_sync(0xffffffffu, uu, __ffs(hb) - 1);
-                if (lane == 0) pull_found(p, L, ws, ws.ls[r], v, hit, bl, el);
-                break;
+#pragma unroll
+            for (int q = 0; q < PULL_LONG_U; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
+#pragma unroll
+            for (int q = 0; q < PULL_LONG_U; ++q) {
+                const unsigned hb = __ballot_sync(0xffffffffu, uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u));
+                if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[q], __ffs(hb) - 1);
             }
         }
+        if (hit >= 0 && lane == 0) pull_found(p, L, ws, ws.ls[r], v, hit, bl, el);
     }
     __syncwarp();
     if (lane == 0) ws.nl = 0;
     __syncwarp();
 }
 
-constexpr int PULL_SLOTS = 2;       // vertices a lane scans at once in a sparse block
-constexpr int PULL_SPARSE_MAX = 384;  // unvisited vertices (of 1024) up to which a block is sparse
+#ifndef BFS_PULL_SLOTS
+#define BFS_PULL_SLOTS 2
+#endif
+#ifndef BFS_PULL_SPARSE_MAX
+#define BFS_PULL_SPARSE_MAX 128
+#endif
+constexpr int PULL_SLOTS = BFS_PULL_SLOTS;  // vertices a lane scans at once in a sparse block
+constexpr int PULL_SPARSE_MAX = BFS_PULL_SPARSE_MAX;  // unvisited vertices (of 1024) up to which a block is sparse
 
 // Pull level (Section 5, loop order d -> s).  Warps take blocks of 32 words
 // of P (1024 vertices) round-robin; block b holds the words b + l * S
@@ -741,37 +862,32 @@ constexpr int PULL_SPARSE_MAX = 384;  // unvisited vertices (of 1024) up to whic
 // registers.  NC selects non-coherent loads of P and F_i, valid when no other
 // CTA writes them during the kernel (the graph-mode kernel); the persistent
 // kernel uses ordinary loads ordered by its grid barrier.
+// The unvisited vertices of the block whose word l (P word pwl) is in lane
+// l: per lane um = ~pwl, excl = unvisited vertices in the words before its
+// own; returns U, their number in the block.  Warp-uniform.
+__device__ __forceinline__ int pull_block_census(unsigned pwl, unsigned& um, int& excl) {
+    um = ~pwl;
+    const int c = __popc(um);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane_id() >= o) incl += y;
+    }
+    excl = incl - c;
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Sparse block: the lane pipeline described above.  Warp-uniform.
 template <bool NC>
-__device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                                           PullWarpSmem& ws) {
+__device__ __forceinline__ void pull_block_sparse(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
+                                                  uint32_t* f_next, PullWarpSmem& ws, long long bi, long long S,
+                                                  long long wl, unsigned pwl, unsigned um, int excl, int U) {
     constexpr unsigned FULL = 0xffffffffu;
     enum { IDLE = 0, BOUNDS = 1, FIRST = 2, TEST = 3 };
     const unsigned lane = lane_id();
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int serial = max(1, min(p.pull_serial, PULL_SERIAL_MAX));
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long S = (p.W + 31) >> 5;
-    for (long long bi = gwarp; bi < S; bi += nwarps) {
-        const long long wl = bi + lane * S;
-        const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
-        const unsigned um = ~pwl;  // unvisited vertices of this lane's word
-        const int c = __popc(um);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if ((int)lane >= o) incl += y;
-        }
-        const int U = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - c;
-        if (U == 0) {  // warp-uniform: every vertex of the block is visited
-            if (wl < p.W) f_next[wl] = 0;
-            continue;
-        }
-        if (U > PULL_SPARSE_MAX) {
-            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl);
-            continue;
-        }
+    {
         ws.nb[lane] = 0;
         if (lane == 0) ws.nl = 0;
         __syncwarp();
@@ -889,7 +1005,150 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
     }
 }
 
+template <bool NC>
+__device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                           PullWarpSmem& ws) {
+    const unsigned lane = lane_id();
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long S = (p.W + 31) >> 5;
+    for (long long bi = gwarp; bi < S; bi += nwarps) {
+        const long long wl = bi + lane * S;
+        const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : 0xffffffffu;
+        unsigned um;
+        int excl;
+        const int U = pull_block_census(pwl, um, excl);
+        if (U == 0) {  // warp-uniform: every vertex of the block is visited
+            if (wl < p.W) f_next[wl] = 0;
+        } else if (U > PULL_SPARSE_MAX && L.pairs_ok) {
+            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl);
+        } else {
+            pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
+        }
+    }
+}
+
+// Pull level with the dense words of a CTA shared by all its warps.  CTA c
+// takes the blocks c, c + G, c + 2G, ... (G CTAs), one per warp per round.  A
+// warp finishes a sparse block itself (pull_block_sparse); a dense block's
+// open words go to a CTA list, which all warps then drain PULL_WPI words at a
+// time through a shared-memory cursor.  The cost of a dense block (the
+// longest scan among the lanes of each group of words) is thereby spread over
+// the CTA's warps instead of being carried by one.  Block-uniform.
+template <bool NC, int T>
+__device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                               PullWarpSmem& ws, PullCtaSmem<T>& cs) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int NW = T / 32;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const long long S = (p.W + 31) >> 5;
+    const long long G = gridDim.x;
+    for (long long r = blockIdx.x; r < S; r += G * NW) {  // CTA-uniform
+        if (threadIdx.x == 0) {
+            cs.n = 0;
+            cs.next = 0;
+        }
+        __syncthreads();
+        const long long bi = r + (long long)warp * G;
+        if (bi < S) {  // warp-uniform
+            const long long wl = bi + lane * S;
+            const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : FULL;
+            unsigned um;
+            int excl;
+            const int U = pull_block_census(pwl, um, excl);
+            if (U == 0) {
+                if (wl < p.W) f_next[wl] = 0;
+            } else if (U <= PULL_SPARSE_MAX || !L.pairs_ok) {
+                pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
+            } else {
+                if (wl < p.W && pwl == FULL) f_next[wl] = 0;
+                const bool add = wl < p.W && pwl != FULL;
+                const unsigned am = __ballot_sync(FULL, add);
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&cs.n, __popc(am));
+                base = __shfl_sync(FULL, base, 0);
+                if (add) {
+                    const int k = base + __popc(am & lanemask_lt());  // < NW * 32 = T
+                    cs.word[k] = (int)wl;
+                    cs.pw[k] = pwl;
+                }
+            }
+        }
+        __syncthreads();
+        const int nlist = cs.n;
+        for (;;) {  // warp-uniform
+            int k0 = 0;
+            if (lane == 0) k0 = atomicAdd(&cs.next, PULL_WPI);
+            k0 = __shfl_sync(FULL, k0, 0);
+            if (k0 >= nlist) break;
+            long long wv[PULL_WPI];
+            unsigned pw[PULL_WPI];
+#pragma unroll
+            for (int k = 0; k < PULL_WPI; ++k) {
+                const bool has = k0 + k < nlist;
+                wv[k] = has ? cs.word[k0 + k] : -1;
+                pw[k] = has ? cs.pw[k0 + k] : FULL;
+            }
+            pull_words<NC>(p, L, f_cur, f_next, wv, pw);
+        }
+        __syncthreads();  // the list is drained before the next round resets it
+    }
+}
+
 // ------------------------------------------------------------ conversions
+// Variant 6 (BFS_SORT_DEVICE): F_i's bitmap -> queue in ascending vertex
+// order over the whole device.  CTA b owns words [b W / G, (b+1) W / G).
+// Phase 1 counts the frontier vertices of each CTA's range into cta_cnt[b];
+// after a grid barrier, phase 2 places each range at the sum of the counts
+// before it and writes its vertices in order (no atomics: the ranges are
+// disjoint).  With units set, chunk units of big rows are appended as in
+// bitmap_to_queue.
+__device__ __forceinline__ void sort_range(const Params1& p, long long& lo, long long& hi) {
+    lo = (long long)blockIdx.x * p.W / gridDim.x;
+    hi = (long long)(blockIdx.x + 1) * p.W / gridDim.x;
+}
+
+template <int T>
+__device__ void sort_count(const Params1& p, TileSmem<T>& sm, const uint32_t* f_cur) {
+    long long lo, hi;
+    sort_range(p, lo, hi);
+    int c = 0;
+    for (long long w = lo + threadIdx.x; w < hi; w += T) c += __popc(__ldcg(f_cur + w));
+    int total;
+    block_exclusive_scan(c, sm.scan_tmp, &total);
+    if (threadIdx.x == 0) p.cta_cnt[blockIdx.x] = (unsigned)total;
+}
+
+template <int T>
+__device__ void sort_emit(const Params1& p, TileSmem<T>& sm, const uint32_t* f_cur, int4* q_cur, int2* u_cur,
+                          Counters* cur, bool units) {
+    long long lo, hi;
+    sort_range(p, lo, hi);
+    unsigned long long before = 0;
+    for (unsigned b = threadIdx.x; b < blockIdx.x; b += T) before += __ldcg(p.cta_cnt + b);
+    before = warp_sum(before);
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = before;
+    __syncthreads();
+    unsigned long long base = 0;
+    for (int i = 0; i < T / 32; ++i) base += sm.red[i];
+    for (long long wb = lo; wb < hi; wb += T) {  // CTA-uniform
+        const long long w = wb + threadIdx.x;
+        unsigned fw = w < hi ? __ldcg(f_cur + w) : 0u;
+        int total;
+        const int off = block_exclusive_scan(__popc(fw), sm.scan_tmp, &total);
+        int r = 0;
+        while (fw) {
+            const int b = __ffs(fw) - 1;
+            fw &= fw - 1;
+            const int v = (int)(w * 32 + b);
+            const int rb = __ldg(p.row_ptr + v), re = __ldg(p.row_ptr + v + 1);
+            q_cur[base + off + r++] = make_int4(v, rb, re, 0);
+            if (units && re - rb >= p.chunk) emit_units(p, u_cur, cur, v, re - rb);
+        }
+        base += (unsigned long long)total;
+    }
+}
+
 // F_i bitmap -> queue Q_i (ascending vertex order inside each CTA chunk) and
 // chunk units for its big rows.  Cursor: cur->conv.
 template <int T>

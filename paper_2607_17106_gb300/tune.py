@@ -4,7 +4,9 @@ Sweeps, on a given graph and seeded sources, the knobs of `bfs_options` that
 change only the schedule (never the result): drive mode, CTA size, chunk-unit
 size, warp threshold, pull flatten width, claim aggregation, the push
 advance / visited-update arrangement (fused, or an edge frontier claimed by a
-filter pass: Variants 13/14 and 20/23 of Section 7.2), and the direction
+filter pass: Variants 13/14 and 20/23 of Section 7.2), the frontier order of
+push-queue levels (claim order, or sorted device-wide or per tile: Variants 6
+and 7), and the direction
 thresholds alpha / beta / gamma; for batched (64-lane) searches the MS-BFS
 knobs.  Each candidate's mean device time per search is measured with
 CUDA events after warm-up; the best is stored in a JSON cache keyed by
@@ -24,7 +26,8 @@ import sys
 
 import numpy as np
 
-from . import BFS_MODE_GRAPH, BFS_MODE_PERSISTENT, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED, BFS_PUSH_FUSED, Graph, options
+from . import (BFS_MODE_GRAPH, BFS_MODE_PERSISTENT, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED, BFS_PUSH_FUSED,
+               BFS_SORT_DEVICE, BFS_SORT_NONE, BFS_SORT_TILE, Graph, options)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(_HERE, "tune_cache.json")
@@ -37,6 +40,7 @@ SINGLE_SPACE = {
     "pull_serial": [8, 16, 32],
     "claim_aggregate": [0, 1],
     "push_filter": [BFS_PUSH_FUSED, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED],
+    "frontier_sort": [BFS_SORT_NONE, BFS_SORT_DEVICE, BFS_SORT_TILE],
     "alpha": [8.0, 14.0, 24.0],
     "beta": [12.0, 24.0, 48.0],
     "gamma": [8.0, 16.0, 64.0],
@@ -92,8 +96,11 @@ def time_candidate(g: Graph, sources, opt, batch: bool, reps: int = 3) -> float:
 
 
 def valid_candidate(cand: dict) -> bool:
-    """Combinations the library accepts: the filter forms need the persistent or host-loop drive."""
-    return not (cand.get("mode") == BFS_MODE_GRAPH and cand.get("push_filter", BFS_PUSH_FUSED) != BFS_PUSH_FUSED)
+    """Combinations the library accepts: the filter forms and the frontier sorts
+    need the persistent or host-loop drive."""
+    if cand.get("mode") != BFS_MODE_GRAPH:
+        return True
+    return cand.get("push_filter", BFS_PUSH_FUSED) == BFS_PUSH_FUSED and cand.get("frontier_sort", BFS_SORT_NONE) == BFS_SORT_NONE
 
 
 def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int = 2, verbose=False):

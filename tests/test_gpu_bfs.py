@@ -266,6 +266,103 @@ def test_push_filter_option_errors(rmat14):
         assert e.value.status == bg.BFS_EINVAL
 
 
+@pytest.mark.parametrize("fs", [bg.BFS_SORT_DEVICE, bg.BFS_SORT_TILE])
+def test_frontier_sort_forms_match_oracle(rmat14, fs):
+    # Variants 6 (device-wide sort through the bitmap) and 7 (per-tile
+    # bitonic sort): push-only, the heuristic, random schedules (queue levels
+    # after pull and after push levels), the host loop, small chunks, and the
+    # other CTA sizes
+    n, adj, g, srcs = rmat14
+    opts = [bg.options(batch=0, frontier_sort=fs, policy=bg.BFS_POLICY_PUSH),
+            bg.options(batch=0, frontier_sort=fs),
+            bg.options(batch=0, frontier_sort=fs, mode=bg.BFS_MODE_HOST_LOOP, chunk=64, medium=4),
+            bg.options(batch=0, frontier_sort=fs, block_threads=512),
+            bg.options(batch=0, frontier_sort=fs, block_threads=256, push_filter=bg.BFS_PUSH_FILTER)]
+    for o in opts:
+        dd, pp = _run(g, n, srcs[:4], o)
+        _check(adj, srcs[:4], dd, pp)
+    rng = np.random.default_rng(23)
+    for t in range(4):
+        sched = rng.integers(0, 3, 30).tolist()
+        s = srcs[t]
+        dd, pp = _run(g, n, [s], bg.options(schedule=sched, batch=0, frontier_sort=fs))
+        _check(adj, [s], dd, pp)
+
+
+@pytest.mark.parametrize("kind", ["grid", "ba", "path", "tiny"])
+def test_frontier_sort_other_families(kind):
+    if kind == "grid":
+        n, s, d = graphgen.grid(128, 96, 0.1, seed=4)
+    elif kind == "ba":
+        n, s, d = graphgen.barabasi_albert(1 << 14, 8, seed=8)
+    elif kind == "path":
+        n = 3000
+        s, d = np.arange(n - 1, dtype=np.int32), np.arange(1, n, dtype=np.int32)
+    else:
+        n = 77
+        s = np.array([0, 1, 2, 40, 41, 76], np.int32)
+        d = np.array([1, 2, 3, 41, 42, 76], np.int32)
+    adj, g = _graph_pair(n, s, d)
+    srcs = graphgen.sample_sources(n, s, d, 3, seed=12) if kind != "tiny" else [0, 5, 40, 76]
+    for fs in (bg.BFS_SORT_DEVICE, bg.BFS_SORT_TILE):
+        for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
+            dd, pp = _run(g, n, srcs, bg.options(batch=0, frontier_sort=fs, policy=pol))
+            _check(adj, srcs, dd, pp)
+
+
+def test_frontier_sort_option_errors(rmat14):
+    n, adj, g, srcs = rmat14
+    for o in (bg.options(batch=0, frontier_sort=3), bg.options(batch=0, frontier_sort=-1),
+              bg.options(batch=0, frontier_sort=bg.BFS_SORT_TILE, mode=bg.BFS_MODE_GRAPH)):
+        with pytest.raises(bg.BfsError) as e:
+            _run(g, n, srcs[:1], o)
+        assert e.value.status == bg.BFS_EINVAL
+
+
+def _barbell():
+    """A 3000-vertex path, an RMAT scale-14 component and a 2000-vertex path in
+    a chain: searches from the path ends run long stretches of tiny levels with
+    a burst of large levels in the middle."""
+    nr, rs, rd = graphgen.rmat(14, 16, seed=21)
+    deg = np.bincount(np.concatenate([rs, rd]), minlength=nr)
+    hub = int(np.argmax(deg))
+    leaf = int(np.flatnonzero(deg == deg[deg > 0].min())[0])
+    a, b = 3000, 2000
+    pa = np.arange(a, dtype=np.int32)
+    pb = np.arange(a + nr, a + nr + b, dtype=np.int32)
+    src = np.concatenate([pa[:-1], rs + a, pb[:-1], [a - 1, a + leaf]]).astype(np.int32)
+    dst = np.concatenate([pa[1:], rd + a, pb[1:], [a + hub, a + nr]]).astype(np.int32)
+    return a + nr + b, src, dst
+
+
+@pytest.mark.parametrize("threads", [1024, 512])
+def test_small_frontier_levels_hand_over_to_the_grid_and_back(threads):
+    # one CTA runs the tiny levels of the paths, the whole grid the RMAT burst
+    n, s, d = _barbell()
+    adj, g = _graph_pair(n, s, d)
+    srcs = [0, n - 1, 3000 + 5, 1500]
+    for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
+        dd, pp = _run(g, n, srcs, bg.options(batch=0, policy=pol, block_threads=threads))
+        _check(adj, srcs, dd, pp)
+    # the level log covers every level, small ones included
+    log = (bg.bfs_level_record * 8192)()
+    nlev = bg.ctypes.c_int32(0)
+    depth = np.empty(n, np.int32)
+    g.run(np.array([0], np.int32), depth, None, bg.options(batch=0, level_log=log, level_log_cap=8192,
+                                                          levels_out=bg.ctypes.pointer(nlev)))
+    ref = oracle.level_stats(adj, depth)
+    assert nlev.value == len(ref)
+    for i in range(nlev.value):
+        assert log[i].level == i and log[i].f == ref[i][0] and log[i].e_f == ref[i][1], i
+    assert log[nlev.value].dir == -1
+    # the level limit is enforced inside a run of small levels
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [0], bg.options(batch=0, max_levels=100))
+    assert e.value.status == bg.BFS_ERANGE
+    dd, pp = _run(g, n, [0], bg.options(batch=0))
+    _check(adj, [0], dd, pp)
+
+
 def test_edge_cases_tiny_and_isolated():
     # one vertex, no edges
     g = bg.Graph.build(1, np.zeros(0, np.int32), np.zeros(0, np.int32))

@@ -43,6 +43,8 @@ def test_coordinate_search_skips_rejected_combinations(monkeypatch):
     assert found == {"mode": bg.BFS_MODE_GRAPH} and t == 80.0
     assert tune.valid_candidate({"push_filter": bg.BFS_PUSH_FILTER})
     assert not tune.valid_candidate({"mode": bg.BFS_MODE_GRAPH, "push_filter": bg.BFS_PUSH_FILTER_PREDICATED})
+    assert tune.valid_candidate({"frontier_sort": bg.BFS_SORT_DEVICE})
+    assert not tune.valid_candidate({"mode": bg.BFS_MODE_GRAPH, "frontier_sort": bg.BFS_SORT_TILE})
 
 
 def test_cache_round_trip(tmp_path, monkeypatch):
