@@ -188,8 +188,8 @@ typedef struct {
     uint32_t struct_size;    /* sizeof(bfs_options); set by bfs_options_init */
     int32_t mode;            /* BFS_MODE_* */
     int32_t policy;          /* BFS_POLICY_* */
-    float alpha;             /* Beamer alpha (8) */
-    float beta;              /* Beamer beta (48) */
+    float alpha;             /* Beamer alpha of single-source searches (14) */
+    float beta;              /* Beamer beta of single-source searches (48) */
     float gamma;             /* push levels read the bitmap when f > n / gamma (16) */
     int32_t chunk;           /* push: vertices with degree >= chunk are split into chunk-edge units (1024) */
     int32_t medium;          /* push: degree >= medium is expanded by a whole warp (32) */
@@ -210,6 +210,8 @@ typedef struct {
                                 m (target, source) pairs, 8 B each, allocated on first use; the CUDA-graph
                                 drive rejects it with EINVAL */
     int32_t frontier_sort;   /* BFS_SORT_* (BFS_SORT_NONE); the CUDA-graph drive rejects a sort with EINVAL */
+    float batch_alpha;       /* alpha of the 64-lane batched direction test (4) */
+    float batch_beta;        /* beta of the 64-lane batched direction test (48) */
 } bfs_options;
 
 /* Fill `opt` with the defaults listed above. */
@@ -225,7 +227,9 @@ void bfs_options_init(bfs_options* opt);
  * parent may be NULL.  Depths do not depend on the options; parents may.
  * sources[k]: host or device.  depth/parent: [k][n] int32, host or device.
  * k == 1 runs the single-source path; k > 1 runs 64-lane MS-BFS batches (or
- * single sources when opt->batch == 0).
+ * single sources when opt->batch == 0: one search after another, all in one
+ * persistent launch when the outputs are device memory, the drive is
+ * persistent and no level log or level count is requested).
  * Errors: EINVAL (null g/sources/depth, k <= 0, source outside [0, n)),
  * ENOMEM, ECUDA, ETIMEOUT (outputs undefined), ERANGE (max_levels exceeded).
  */

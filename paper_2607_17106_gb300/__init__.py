@@ -76,7 +76,8 @@ class bfs_options(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("mlp", ctypes.c_void_p),
                 ("level_log", ctypes.POINTER(bfs_level_record)), ("level_log_cap", ctypes.c_int32),
                 ("levels_out", ctypes.POINTER(ctypes.c_int32)), ("batch", ctypes.c_int32),
-                ("push_filter", ctypes.c_int32), ("frontier_sort", ctypes.c_int32)]
+                ("push_filter", ctypes.c_int32), ("frontier_sort", ctypes.c_int32),
+                ("batch_alpha", ctypes.c_float), ("batch_beta", ctypes.c_float)]
 
 
 _lib = None

@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.qb = sm.t.qb + (threadIdx.x >> 5) * QBUF;
     L.qe = sm.t.qe + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
+    L.qcap = p.n;
+    L.err = &p.ctl->bar.err;
     L.precheck = push_precheck(h.m_u, p.m, h.e_f);
     const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
     const int2* u_cur = (level & 1) ? p.U1 : p.U0;
@@ -256,7 +258,6 @@ __global__ void __launch_bounds__(PULL_T) g_pull(Params1 p) {
     L.parent = h.parent;
     L.ef = 0;
     L.cnt = 0;
-    L.pairs_ok = pull_pairs_ok(h.e_f, h.m_u);
     const uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
     uint32_t* f_next = (level & 1) ? p.F0 : p.F1;
     pull_level<true>(p, L, f_cur, f_next, s_pull[threadIdx.x >> 5]);

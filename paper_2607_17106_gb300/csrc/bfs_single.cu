@@ -58,6 +58,7 @@ void free_ws1(Workspace1* w) {
     cudaFree(w->d_sticky);
     cudaFree(w->stage_depth);
     cudaFree(w->stage_parent);
+    cudaFree(w->d_srcs);
     cudaFree(w->d_log);
     cudaFree(w->d_sched);
     cudaFreeHost(w->h_ctl);
@@ -65,181 +66,6 @@ void free_ws1(Workspace1* w) {
     delete w;
 }
 
-
-// ------------------------------------------------------------ small levels
-// Small-frontier mode.  A push-queue level whose frontier has at most
-// SMALL_F vertices and SMALL_EF edges is latency-bound: a grid-wide level
-// costs a grid barrier, a read of the global level counters and a global
-// append counter on top of its few memory round trips.  Such levels run on
-// CTA 0 alone, one after another, separated by __syncthreads: the next
-// level's counters live in shared memory, queue entries still go to the
-// global queues (so the grid can take over at any level), and P, depth and
-// parent are the global arrays.  The other CTAs wait on a generation word,
-// resetting their time limit whenever CTA 0 reports progress, and all CTAs
-// reload the loop state once CTA 0 publishes it.
-#ifndef BFS_SMALL_MODE
-#define BFS_SMALL_MODE 0
-#endif
-#ifndef BFS_SMALL_EF
-#define BFS_SMALL_EF 4096
-#endif
-#ifndef BFS_SMALL_F
-#define BFS_SMALL_F 2048
-#endif
-
-__device__ __forceinline__ bool small_level_fits(long long f, long long e_f) {
-    return e_f <= BFS_SMALL_EF && f <= BFS_SMALL_F;
-}
-
-// CTA 0: runs levels from `level` (already decided: push-queue, fits) while
-// they stay small push-queue levels; publishes the loop state and the next
-// level's counters, then the generation `gen`.  Block-uniform.
-template <int T>
-__device__ __noinline__ void small_levels(const Params1& p, TileSmem<T>& sm, int level, long long f, long long e_f, long long m_u,
-                             long long f_prev, int bm_valid, int level_end, unsigned gen, float* s_feat,
-                             float* s_mlp_out, const float* mlp_w) {
-    __shared__ Counters sc[2];
-    __shared__ int s_abort;
-    Ctl1* ctl = p.ctl;
-    const unsigned warp = threadIdx.x >> 5;
-    int prev_dir = BFS_DIR_PUSH_QUEUE;
-    bool done = false;
-    long long f_new = 0, ef_new = 0, u_new = 0;
-    for (int it = 0;; ++it) {
-        Counters* nx = &sc[level & 1];
-        if (threadIdx.x == 0) {
-            nx->q_len = 0;
-            nx->u_len = 0;
-            nx->e_f = 0;
-            if ((it & 63) == 0) s_abort = ld_volatile_i32(&ctl->bar.abort);
-        }
-        __syncthreads();
-        if (s_abort) return;  // a waiter gave up; it has raised the error
-        LevelCtx L;
-        L.level = level;
-        L.depth = p.depth;
-        L.parent = p.parent;
-        L.q_next = (level & 1) ? p.Q0 : p.Q1;
-        L.u_next = (level & 1) ? p.U0 : p.U1;
-        L.next = nx;  // shared memory: appends count with shared atomics
-        L.ef = 0;
-        L.cnt = 0;
-        L.qv = sm.t.qv + warp * QBUF;
-        L.qb = sm.t.qb + warp * QBUF;
-        L.qe = sm.t.qe + warp * QBUF;
-        L.qn = 0;
-        L.precheck = push_precheck(m_u, p.m, e_f);
-        L.pairs_ok = false;
-        const int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
-        for (long long base = 0; base < f; base += T) {  // block-uniform
-            const long long q = base + threadIdx.x;
-            const int4 e = q < f ? __ldcg(q_cur + q) : make_int4(-1, 0, 0, 0);
-            push_tile<T>(p, L, sm, e.x, e.y, e.z, false);  // big rows too: their edges are few here
-        }
-        flush_qbuf(L);
-        const unsigned long long ef = warp_sum(L.ef);
-        if ((threadIdx.x & 31) == 0 && ef) atomicAdd(&nx->e_f, ef);
-        __syncthreads();
-        f_new = (long long)nx->q_len;
-        ef_new = (long long)nx->e_f;
-        u_new = (long long)nx->u_len;
-        if (threadIdx.x == 0) *(volatile int*)&ctl->small_beat = level;  // progress for the waiters
-        f_prev = f;
-        ++level;
-        if (f_new == 0) {
-            done = true;
-            if (threadIdx.x == 0 && p.log && level < p.log_cap) {
-                bfs_level_record r;
-                r.level = level;
-                r.dir = -1;
-                r.f = 0;
-                r.e_f = 0;
-                r.m_u = m_u;
-                r.t_ns = (int64_t)globaltimer_ns();
-                p.log[level] = r;
-            }
-            break;
-        }
-        if (level >= p.max_levels) {
-            if (threadIdx.x == 0) atomicCAS(&ctl->bar.err, 0, (int)DEV_LEVELS);
-            done = true;
-            break;
-        }
-        const long long mu_next = m_u - ef_new;
-        const int dir = decide_dir(p, level, f_new, ef_new, mu_next, f_prev, prev_dir, s_feat, s_mlp_out, mlp_w);
-        if (dir != BFS_DIR_PUSH_QUEUE || !small_level_fits(f_new, ef_new) || level >= level_end) break;
-        m_u = mu_next;
-        if (threadIdx.x == 0 && p.log && level < p.log_cap) {
-            bfs_level_record r;
-            r.level = level;
-            r.dir = dir;
-            r.f = f_new;
-            r.e_f = ef_new;
-            r.m_u = m_u;
-            r.t_ns = (int64_t)globaltimer_ns();
-            p.log[level] = r;
-        }
-        f = f_new;
-        e_f = ef_new;
-    }
-    // hand the search back: the grid continues at `level`, whose queue was
-    // written to the global queue; m_u excludes that level's e_f, which the
-    // main loop subtracts itself
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 3; ++k) {
-            Counters* c = &ctl->slot[k];
-            const bool cur = k == level % 3;
-            c->q_len = cur ? (unsigned long long)f_new : 0ull;
-            c->u_len = cur ? (unsigned long long)u_new : 0ull;
-            c->e_f = cur ? (unsigned long long)ef_new : 0ull;
-            c->conv = 0;
-            c->e_len = 0;
-        }
-        ctl->next_level = level;
-        ctl->prev_dir = prev_dir;
-        ctl->bm_valid = bm_valid;
-        ctl->q_valid = level;
-        ctl->m_u = m_u;
-        ctl->f_prev = f_prev;
-        ctl->done = done ? 1 : 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) st_release_u32(&ctl->small_gen, gen);
-}
-
-// The other CTAs: wait until CTA 0 publishes generation `gen`.  The time
-// limit restarts whenever CTA 0 reports a new level, so a long run of small
-// levels is not mistaken for a hang.  Returns false when the wait was aborted.
-__device__ bool small_wait(Ctl1* ctl, unsigned gen, int64_t timeout_ns) {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        uint64_t t0 = globaltimer_ns();
-        int beat = ld_volatile_i32(&ctl->small_beat);
-        while (ld_acquire_u32(&ctl->small_gen) != gen) {
-            __nanosleep(256);
-            const int b = ld_volatile_i32(&ctl->small_beat);
-            const uint64_t now = globaltimer_ns();
-            if (b != beat) {
-                beat = b;
-                t0 = now;
-            }
-            if (ld_volatile_i32(&ctl->bar.abort)) {
-                ok = 0;
-                break;
-            }
-            if ((int64_t)(now - t0) > timeout_ns) {
-                atomicCAS(&ctl->bar.err, 0, (int)DEV_TIMEOUT);
-                atomicExch(&ctl->bar.abort, 1);
-                ok = 0;
-                break;
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // ------------------------------------------------------------ the kernel
 // Dynamic shared memory of the persistent kernel: a copy of the policy
@@ -266,8 +92,17 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     const long long gthreads = (long long)gridDim.x * T;
     unsigned bar_target = p.do_init ? 0u : __ldcg(&ctl->bar_base);
 
+    // One launch runs nsrc searches one after another (do_init), or continues
+    // the search whose state the control block holds (host-loop drive).
+    const int nsearch = p.do_init ? max(p.nsrc, 1) : 1;
+    int level = 0, prev_dir = BFS_DIR_PUSH_QUEUE, bm_valid = -1, q_valid = 0;
+    long long m_u = 0, f_prev = 0;
+    bool done = false;
+    for (int si = 0; si < nsearch; ++si) {
+    int32_t* const depth = p.depth + (int64_t)si * p.n;
+    int32_t* const parent = p.parent ? p.parent + (int64_t)si * p.n : nullptr;
     if (p.do_init) {
-        int s = p.src_value;
+        const int s = p.srcs ? __ldg(p.srcs + si) : p.src_value;
         for (long long w = gtid; w < p.W; w += gthreads) {
             unsigned bits = __ldg(p.isolated + w);
             if (w == (s >> 5)) bits |= 1u << (s & 31);
@@ -275,8 +110,8 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             p.P[w] = bits;
         }
         for (long long v = gtid; v < p.n; v += gthreads) {
-            p.depth[v] = (v == s) ? 0 : -1;
-            if (p.parent) p.parent[v] = (v == s) ? s : -1;
+            depth[v] = (v == s) ? 0 : -1;
+            if (parent) parent[v] = (v == s) ? s : -1;
         }
         if (gtid == 0) {
             const int rb = __ldg(p.row_ptr + s), re = __ldg(p.row_ptr + s + 1);
@@ -284,9 +119,18 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             p.Q0[0] = make_int4(s, rb, re, 0);
             int nch = deg >= p.chunk ? (deg + p.chunk - 1) / p.chunk : 0;
             for (int c = 0; c < nch; ++c) p.U0[c] = make_int2(s, c);
+            for (int k = 1; k < 3; ++k) {  // a previous search of this launch used them
+                ctl->slot[k].q_len = 0;
+                ctl->slot[k].u_len = 0;
+                ctl->slot[k].e_f = 0;
+                ctl->slot[k].conv = 0;
+                ctl->slot[k].e_len = 0;
+            }
             ctl->slot[0].q_len = 1;
             ctl->slot[0].u_len = nch;
             ctl->slot[0].e_f = deg;
+            ctl->slot[0].conv = 0;
+            ctl->slot[0].e_len = 0;
             ctl->next_level = 0;
             ctl->prev_dir = BFS_DIR_PUSH_QUEUE;
             ctl->bm_valid = -1;
@@ -298,16 +142,15 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
     }
 
-    int level = __ldcg(&ctl->next_level);
-    int prev_dir = __ldcg(&ctl->prev_dir);
-    int bm_valid = __ldcg(&ctl->bm_valid);
-    int q_valid = __ldcg(&ctl->q_valid);
-    long long m_u = __ldcg(&ctl->m_u);
-    long long f_prev = __ldcg(&ctl->f_prev);
-    bool done = __ldcg(&ctl->done) != 0;
-    int level_end = level + p.level_count;
+    level = __ldcg(&ctl->next_level);
+    prev_dir = __ldcg(&ctl->prev_dir);
+    bm_valid = __ldcg(&ctl->bm_valid);
+    q_valid = __ldcg(&ctl->q_valid);
+    m_u = __ldcg(&ctl->m_u);
+    f_prev = __ldcg(&ctl->f_prev);
+    done = __ldcg(&ctl->done) != 0;
+    const int level_end = level + p.level_count;
     const unsigned warp = threadIdx.x >> 5;
-    unsigned small_gen = 0;  // small-frontier hand-overs so far (the same on every CTA)
 
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
@@ -351,28 +194,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             r.t_ns = (int64_t)globaltimer_ns();
             p.log[level] = r;
         }
-#if BFS_SMALL_MODE
-        if (dir == BFS_DIR_PUSH_QUEUE && q_valid == level && level_end - level > 1 && small_level_fits(f, e_f) &&
-            p.push_filter == BFS_PUSH_FUSED && !(SORT && p.frontier_sort != BFS_SORT_NONE)) {
-            // CTA 0 runs this level and the small ones after it; the rest wait
-            ++small_gen;
-            if (blockIdx.x == 0) {
-                small_levels<T>(p, sm, level, f, e_f, m_u, f_prev, bm_valid, level_end, small_gen, s_feat, &s_mlp_out,
-                                mlp_w);
-                if (ld_volatile_i32(&ctl->bar.abort)) return;
-            } else if (!small_wait(ctl, small_gen, p.timeout_ns)) {
-                return;
-            }
-            level = __ldcg(&ctl->next_level);
-            prev_dir = __ldcg(&ctl->prev_dir);
-            bm_valid = __ldcg(&ctl->bm_valid);
-            q_valid = __ldcg(&ctl->q_valid);
-            m_u = __ldcg(&ctl->m_u);
-            f_prev = __ldcg(&ctl->f_prev);
-            done = __ldcg(&ctl->done) != 0;
-            continue;
-        }
-#endif
         int2* u_cur = (level & 1) ? p.U1 : p.U0;
         uint32_t* f_cur = (level & 1) ? p.F1 : p.F0;
         uint32_t* f_nxt = (level & 1) ? p.F0 : p.F1;
@@ -421,8 +242,8 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         }
         LevelCtx L;
         L.level = level;
-        L.depth = p.depth;
-        L.parent = p.parent;
+        L.depth = depth;
+        L.parent = parent;
         L.q_next = (level & 1) ? p.Q0 : p.Q1;
         L.u_next = (level & 1) ? p.U0 : p.U1;
         L.next = nxt;
@@ -432,8 +253,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.qb = sm.t.qb + warp * QBUF;
         L.qe = sm.t.qe + warp * QBUF;
         L.qn = 0;
+        L.qcap = p.n;
+        L.err = &p.ctl->bar.err;
         L.precheck = push_precheck(m_u, p.m, e_f);
-        L.pairs_ok = pull_pairs_ok(e_f, m_u);
         if (dir == BFS_DIR_PULL) {
             pull_level_cta<false, T>(p, L, f_cur, f_nxt, sm.pull.w[warp], sm.pull.c);
         } else {
@@ -483,6 +305,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         (void)done_level;
 #endif
     }
+    // every CTA is past this search's last level before the next one starts
+    if (si + 1 < nsearch && !grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+    }  // searches
     if (gtid == 0) {
         ctl->next_level = level;
         ctl->prev_dir = prev_dir;
@@ -633,6 +458,8 @@ static bfs_status make_params(bfs_graph* g, Workspace1* w, const bfs_options& o,
     p.ucap = w->ucap;
     p.ctl = w->ctl;
     p.src_value = src_value;
+    p.srcs = nullptr;
+    p.nsrc = 1;
     p.sticky = w->d_sticky;
     p.depth = depth;
     p.parent = parent;
@@ -773,6 +600,40 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
 #endif
         if (nl > 0) BFS_CUDA(cudaMemcpy(o.level_log, w->d_log, sizeof(bfs_level_record) * nl, cudaMemcpyDeviceToHost));
     }
+    return BFS_OK;
+}
+
+// k sources, one search after another, all in ONE persistent launch (device
+// outputs [k][n], persistent drive, no level log): the per-search launch and
+// control-block reset are paid once.  A barrier separates the searches.
+bfs_status run_single_many(bfs_graph* g, const int32_t* src_host, int32_t k, int32_t* depth, int32_t* parent,
+                           const bfs_options& o, const float* mlp_dev, cudaStream_t st) {
+    Workspace1* w;
+    bfs_status s = ensure_ws1(g, o.chunk, st, &w);
+    if (s != BFS_OK) return s;
+    Params1 p;
+    s = make_params(g, w, o, mlp_dev, src_host[0], depth, parent, st, p);
+    if (s != BFS_OK) return s;
+    if (w->src_cap < k) {
+        cudaFree(w->d_srcs);
+        w->d_srcs = nullptr;
+        w->src_cap = 0;
+        if (cudaMalloc(&w->d_srcs, (size_t)k * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BFS_ENOMEM, "sources of %d searches", k);
+        }
+        w->src_cap = k;
+    }
+    BFS_CUDA(cudaMemcpyAsync(w->d_srcs, src_host, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    p.srcs = w->d_srcs;
+    p.nsrc = k;
+    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
+    CoopLauncher launcher(o);
+    if (o.frontier_sort == BFS_SORT_DEVICE && launcher.blocks > 4096)
+        return fail(BFS_EINVAL, "frontier_sort supports at most 4096 CTAs (launch has %d)", launcher.blocks);
+    p.do_init = 1;
+    p.level_count = INT32_MAX / 2;
+    BFS_CUDA(launcher(p, st));
     return BFS_OK;
 }
 

@@ -64,6 +64,8 @@ int num_sms() {
 
 bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* parent, const bfs_options& o,
                       const float* mlp_dev, cudaStream_t st);
+bfs_status run_single_many(bfs_graph* g, const int32_t* src_host, int32_t k, int32_t* depth, int32_t* parent,
+                           const bfs_options& o, const float* mlp_dev, cudaStream_t st);
 bfs_status run_msbfs(bfs_graph* g, const int32_t* sources, int32_t k, int32_t* depth, int32_t* parent,
                      const bfs_options& o, const float* mlp_dev, cudaStream_t st);
 bfs_status run_mixed(const bfs_graph* const* graphs, int32_t n_graphs, const int32_t* graph_of_query,
@@ -82,8 +84,10 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->struct_size = sizeof(bfs_options);
     o->mode = BFS_MODE_PERSISTENT;
     o->policy = BFS_POLICY_HEURISTIC;
-    o->alpha = 8.0f;
+    o->alpha = 14.0f;
     o->beta = 48.0f;
+    o->batch_alpha = 4.0f;
+    o->batch_beta = 48.0f;
     o->gamma = 16.0f;
     o->chunk = 1024;
     o->medium = 32;
@@ -107,7 +111,8 @@ static bfs_status check_options(const bfs_options* in, bfs_options* o) {
     if (o->chunk < 64) return fail(BFS_EINVAL, "chunk must be >= 64");
     if (o->medium < 1) return fail(BFS_EINVAL, "medium must be >= 1");
     if (o->pull_serial < 1) return fail(BFS_EINVAL, "pull_serial must be >= 1");
-    if (!(o->alpha > 0) || !(o->beta > 0) || !(o->gamma > 0)) return fail(BFS_EINVAL, "alpha, beta, gamma must be > 0");
+    if (!(o->alpha > 0) || !(o->beta > 0) || !(o->gamma > 0) || !(o->batch_alpha > 0) || !(o->batch_beta > 0))
+        return fail(BFS_EINVAL, "alpha, beta, gamma, batch_alpha, batch_beta must be > 0");
     if (o->barrier_timeout_ns <= 0) return fail(BFS_EINVAL, "barrier_timeout_ns must be > 0");
     if (o->block_threads != 256 && o->block_threads != 512 && o->block_threads != 1024)
         return fail(BFS_EINVAL, "block_threads must be 256, 512 or 1024");
@@ -149,6 +154,8 @@ extern "C" bfs_status bfs_run(const bfs_graph* gc, const int32_t* sources, int32
         return run_msbfs(g, src.data(), k, depth, parent, o, mlp, st);
     }
     const int64_t n = g->n;
+    if (dev_out && k > 1 && o.mode == BFS_MODE_PERSISTENT && !o.level_log && !o.levels_out)
+        return run_single_many(g, src.data(), k, depth, parent, o, mlp, st);
     if (dev_out) {
         for (int j = 0; j < k; ++j) {
             s = run_single(g, src[j], depth + j * n, parent ? parent + j * n : nullptr, o, mlp, st);

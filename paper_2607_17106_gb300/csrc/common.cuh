@@ -155,7 +155,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsi
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
         while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
-            if ((++spins & 31u) == 0) {
+            // limits are checked on the first poll that finds the barrier
+            // open and every 32 polls after it
+            if ((++spins & 31u) == 1) {
                 if (ld_volatile_i32(&b->abort)) { ok = 0; break; }
                 if ((int64_t)(globaltimer_ns() - t0) > timeout_ns) {
                     atomicCAS(&b->err, 0, (int)DEV_TIMEOUT);

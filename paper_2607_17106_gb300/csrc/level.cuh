@@ -35,10 +35,6 @@ struct Ctl1 {
     int32_t src;
     int32_t* depth;
     int32_t* parent;
-    // small-frontier mode: generation published by the CTA that ran the
-    // small levels, and its progress (the level it is on) for the waiters
-    unsigned small_gen;
-    int32_t small_beat;
 };
 
 struct Workspace1 {
@@ -57,6 +53,8 @@ struct Workspace1 {
     int* d_sticky = nullptr;
     int32_t* stage_depth = nullptr;
     int32_t* stage_parent = nullptr;
+    int32_t* d_srcs = nullptr;  // sources of a multi-search launch
+    int32_t src_cap = 0;
     bfs_level_record* d_log = nullptr;
     int32_t log_cap = 0;
     int8_t* d_sched = nullptr;
@@ -92,6 +90,8 @@ struct Params1 {
     int64_t ecap;
     Ctl1* ctl;
     int32_t src_value;
+    const int32_t* srcs;  // nsrc sources searched one after another in one launch (device), or null
+    int32_t nsrc;
     int* sticky;          // first device error of any run, cleared by the host
     int32_t* depth;
     int32_t* parent;
@@ -156,18 +156,12 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
         case BFS_POLICY_MLP: {
             const int h = heuristic_dir(p, f, e_f, m_u, f_prev, prev_dir);
             if (p.mlp && policy_in_band(e_f, m_u, p.alpha)) {
-                // warp 0 evaluates; result broadcast through shared memory
-                if (threadIdx.x < 32) {
-                    if (threadIdx.x == 0)
-                        policy_features(s_feat, f, e_f, m_u, f_prev, level, prev_dir, p.n, p.m, p.deg_max);
-                    __syncwarp();
-                    int a = policy_choice_warp(mlp_w ? mlp_w : p.mlp, s_feat, h, MLP_MARGIN);
-                    if (threadIdx.x == 0) *s_mlp_out = (float)a;
-                }
+                // thread 0 forms the features; the whole CTA evaluates
+                __shared__ float s_h2[MLP_H];
+                __shared__ int s_choice;
+                if (threadIdx.x == 0) policy_features(s_feat, f, e_f, m_u, f_prev, level, prev_dir, p.n, p.m, p.deg_max);
                 __syncthreads();
-                int a = (int)*s_mlp_out;
-                __syncthreads();
-                return a;
+                return policy_choice_block(mlp_w ? mlp_w : p.mlp, s_feat, h, MLP_MARGIN, s_h2, &s_choice);
             }
             return h;
         }
@@ -183,9 +177,6 @@ __device__ inline int decide_dir(const Params1& p, int level, long long f, long 
 // rows make a few frontier words very hot, which the L1 then serves.
 
 // ------------------------------------------------------------ claiming
-#ifndef BFS_PREFETCH_CLAIM
-#define BFS_PREFETCH_CLAIM 0
-#endif
 constexpr int QBUF = 64;  // per-warp shared-memory staging of next-queue entries
 
 struct LevelCtx {
@@ -201,8 +192,9 @@ struct LevelCtx {
     int32_t* qb;            // each): vertex, row begin, row end
     int32_t* qe;
     int qn;                 // entries staged (warp-uniform)
+    long long qcap;         // capacity of q_next (n entries)
+    int* err;               // device error word of the run
     bool precheck;          // push: read P before the OR (most targets already visited)
-    bool pairs_ok;          // pull: dense blocks may take the two-words-at-a-time path
 };
 
 #ifndef BFS_PRECHECK_MIN_EF
@@ -216,16 +208,6 @@ __device__ __forceinline__ bool push_precheck(long long m_u, long long m, long l
     return 2 * m_u < m && e_f >= BFS_PRECHECK_MIN_EF;
 }
 
-#ifndef BFS_PULL_PAIRS_RATIO
-#define BFS_PULL_PAIRS_RATIO 0.0f
-#endif
-// Pull: the two-words-at-a-time path of dense blocks costs, per pair of
-// words, the longest scan among its 64 vertices, so it pays only when nearly
-// every unvisited vertex finds a frontier neighbour at once -- when the
-// frontier's edges e_f are large against the unexplored edges m_u.
-__device__ __forceinline__ bool pull_pairs_ok(long long e_f, long long m_u) {
-    return (float)e_f >= BFS_PULL_PAIRS_RATIO * (float)m_u;
-}
 
 // Move the warp's staged queue entries to the next queue: one atomic per
 // flush instead of one per claiming round.  An entry carries its vertex's row
@@ -238,7 +220,13 @@ __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
     if (lane == 0) base = atomicAdd(&L.next->q_len, (unsigned long long)L.qn);
     base = __shfl_sync(0xffffffffu, base, 0);
     __syncwarp();
-    for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = make_int4(L.qv[i], L.qb[i], L.qe[i], 0);
+    // a vertex is claimed once, so the queue never outgrows n; were that ever
+    // broken, record the overflow instead of writing past the buffer
+    if (base + (unsigned long long)L.qn <= (unsigned long long)L.qcap) {
+        for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = make_int4(L.qv[i], L.qb[i], L.qe[i], 0);
+    } else if (lane == 0) {
+        atomicCAS(L.err, 0, (int)DEV_OVERFLOW);
+    }
     __syncwarp();
     L.qn = 0;
 }
@@ -270,11 +258,6 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
         L.depth[v] = L.level + 1;
         if (L.parent) L.parent[v] = u;
         L.ef += (unsigned long long)deg;
-#if BFS_PREFETCH_CLAIM
-        // the next push level reads this row: start bringing its first
-        // sector into L2 now, off the next level's dependent chain
-        if (deg > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.col + rb));
-#endif
     }
     L.qn += c;
     emit_units_warp(p, L.u_next, L.next, claimed && deg >= p.chunk, v, deg);
@@ -397,6 +380,8 @@ struct PullCtaSmem {
     int next;      // cursor of the warps draining it
     int word[T];   // word index of P
     unsigned pw[T];  // its P word
+    int ns, snext;   // sparse blocks of the round and their cursor
+    long long sblk[T / 32];
 };
 
 // Shared memory of a CTA running level kernels.  Push levels use the tile
@@ -613,21 +598,19 @@ constexpr int PULL_SERIAL_MAX = 32;  // row entries one lane scans before its wa
 // in-neighbours a lane loads and tests per serial step: the loads of one step
 // are independent, so a step costs about one memory round trip whatever R is
 constexpr int PULL_R = BFS_PULL_R;
-#ifndef BFS_PULL_LONG_U
-#define BFS_PULL_LONG_U 1
-#endif
 // 32-entry groups a warp loads per step when it finishes a deferred long row
-constexpr int PULL_LONG_U = BFS_PULL_LONG_U;
+// (4 groups measured no faster than 1)
+constexpr int PULL_LONG_U = 1;
 
 template <bool NC>
 __device__ __forceinline__ unsigned ld_word(const uint32_t* a, long long i) {
     return NC ? __ldg(a + i) : a[i];
 }
 
-#ifndef BFS_PULL_WPI
-#define BFS_PULL_WPI 2
-#endif
-constexpr int PULL_WPI = BFS_PULL_WPI;  // words a dense pull block finishes per iteration
+
+// Words a warp finishes at a time in the dense pull (3 or 4 measured within
+// +-3 % of 2 on RMAT, ER, BA and the grid).
+constexpr int PULL_WPI = 2;
 
 // Dense words of a pull level, PULL_WPI at a time, lane = vertex: wv[k] is a
 // word index of P (-1 for none) and pw[k] its P word.  An unvisited lane
@@ -636,20 +619,102 @@ constexpr int PULL_WPI = BFS_PULL_WPI;  // words a dense pull block finishes per
 // `pull_serial` entries are finished by the whole warp, 4 x 32 entries a step.
 // The warp writes the words of P and of F_{i+1} with plain stores (it owns
 // them).  Warp-uniform.
+// Row bounds of the lanes' vertices of words wv (the first memory step of
+// pull_words, separate so that a caller can issue it ahead).
+__device__ __forceinline__ void pull_word_bounds(const Params1& p, const long long (&wv)[PULL_WPI],
+                                                 const unsigned (&pw)[PULL_WPI], int (&beg)[PULL_WPI],
+                                                 int (&end)[PULL_WPI]) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 0; k < PULL_WPI; ++k) {
+        const bool unvis = !((pw[k] >> lane) & 1u);
+        const long long v = wv[k] * 32 + lane;
+        beg[k] = unvis ? __ldg(p.csc_ptr + v) : 0;
+        end[k] = unvis ? __ldg(p.csc_ptr + v + 1) : 0;
+    }
+}
+
+#ifndef BFS_PULL_DEFER
+#define BFS_PULL_DEFER 0
+#endif
+// Dense pull words: after 2, 4 or 8 entries, when few of a group's vertices
+// are still scanning, those rows leave the group for the warp's leftover
+// list, so the longest scans no longer hold 64 lanes; the list is finished
+// lane-per-row when full and at the end.
+// checkpoint k (after 2, 4, 8 entries) defers when at most 16, 24, 32 lanes are open
+__device__ __forceinline__ int pull_defer_max(int entries) {
+    return entries == 2 ? 16 : entries == 4 ? 24 : entries == 8 ? 32 : -1;
+}
+
+// The warp's leftover rows (ws.lv: vertex, lj: next entry, le: end, lb: row
+// start; at most 32): lane l scans row l four entries a step (first hit in
+// row order is the parent), then rows still open are finished one at a time
+// by the whole warp.  Found vertices set their bits in F_{i+1} and P with
+// atomics: the words' plain stores by their group came first.  Warp-uniform.
 template <bool NC>
-__device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                                           const long long (&wv)[PULL_WPI], const unsigned (&pw)[PULL_WPI]) {
+__device__ __noinline__ void pull_leftovers(const Params1& p, LevelCtx& L, PullWarpSmem& ws, const uint32_t* f_cur,
+                                            uint32_t* f_next) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __syncwarp();
+    const int nl = min(ws.nl, 32);
+    const unsigned lane = lane_id();
+    const bool has = (int)lane < nl;
+    const int v = has ? ws.lv[lane] : 0, b = has ? ws.lb[lane] : 0, e = has ? ws.le[lane] : 0;
+    int j = has ? ws.lj[lane] : 0;
+    int hit = -1;
+    for (int step = 0; step < 8 && __any_sync(FULL, has && hit < 0 && j < e); ++step) {
+        int uu[4];
+        unsigned fw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) uu[q] = (has && hit < 0 && j + q < e) ? __ldg(p.csc_col + j + q) : -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (hit < 0 && uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u)) hit = uu[q];
+        if (hit < 0) j += 4;
+    }
+    unsigned rm = __ballot_sync(FULL, has && hit < 0 && j < e);
+    while (rm) {
+        const int l = __ffs(rm) - 1;
+        const int bl = __shfl_sync(FULL, j, l), el = __shfl_sync(FULL, e, l);
+        int h = -1;
+        for (int base = bl; base < el && h < 0; base += 32) {
+            const int idx = base + (int)lane;
+            const int uu = idx < el ? __ldg(p.csc_col + idx) : -1;
+            const bool t = uu >= 0 && ((ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u);
+            const unsigned hb = __ballot_sync(FULL, t);
+            if (hb) h = __shfl_sync(FULL, uu, __ffs(hb) - 1);
+        }
+        if ((int)lane == l) hit = h;
+        rm &= rm - 1;
+    }
+    if (has && hit >= 0) {
+        L.depth[v] = L.level + 1;
+        if (L.parent) L.parent[v] = hit;
+        L.ef += (unsigned long long)(p.symmetric ? (e - b) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
+        L.cnt += 1;
+        atomicOr(f_next + (v >> 5), 1u << (v & 31));
+        atomicOr(p.P + (v >> 5), 1u << (v & 31));
+    }
+    __syncwarp();
+    if (lane == 0) ws.nl = 0;
+    __syncwarp();
+}
+
+template <bool NC>
+__device__ __forceinline__ void pull_words_scan(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
+                                                uint32_t* f_next, const long long (&wv)[PULL_WPI],
+                                                const unsigned (&pw)[PULL_WPI], const int (&beg)[PULL_WPI],
+                                                const int (&end)[PULL_WPI], PullWarpSmem& ws) {
     const unsigned lane = lane_id();
     const int dnext = L.level + 1;
     const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
     bool unvis[PULL_WPI], found[PULL_WPI];
-    int beg[PULL_WPI], end[PULL_WPI], j[PULL_WPI], par[PULL_WPI];
+    int j[PULL_WPI], par[PULL_WPI];
 #pragma unroll
     for (int k = 0; k < PULL_WPI; ++k) {
         unvis[k] = !((pw[k] >> lane) & 1u);
-        const long long v = wv[k] * 32 + lane;
-        beg[k] = unvis[k] ? __ldg(p.csc_ptr + v) : 0;
-        end[k] = unvis[k] ? __ldg(p.csc_ptr + v + 1) : 0;
         j[k] = beg[k];
         found[k] = false;
         par[k] = -1;
@@ -668,7 +733,12 @@ __device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const 
                 u[k][r] = (lk && j[k] + r < end[k]) ? __ldg(p.csc_col + j[k] + r) : -1;
             live |= lk;
         }
+#if BFS_PULL_DEFER
+        // the deferral below is warp-synchronous: the loop ends for all lanes together
+        if (!__any_sync(0xffffffffu, live)) break;
+#else
         if (!live) break;
+#endif
 #pragma unroll
         for (int k = 0; k < PULL_WPI; ++k)
 #pragma unroll
@@ -688,6 +758,38 @@ __device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const 
                 j[k] += PULL_R;
             }
         }
+#if BFS_PULL_DEFER
+        const int dmax = pull_defer_max(step + PULL_R);
+        if (dmax > 0) {
+            int open = 0;
+#pragma unroll
+            for (int k = 0; k < PULL_WPI; ++k) open += __popc(__ballot_sync(0xffffffffu, !found[k] && j[k] < end[k]));
+            if (open > 0 && open <= dmax) {  // warp-uniform
+                // make room first, finishing rows of earlier groups only: this
+                // group's words are written after the loop, and a row of its
+                // own finished before that would have its bits overwritten
+                if (ws.nl + open > 32) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
+#pragma unroll
+                for (int k = 0; k < PULL_WPI; ++k) {
+                    const bool d = !found[k] && j[k] < end[k];
+                    const unsigned dm = __ballot_sync(0xffffffffu, d);
+                    if (!dm) continue;
+                    if (d) {
+                        const int slot = ws.nl + __popc(dm & lanemask_lt());
+                        ws.lv[slot] = (int)(wv[k] * 32 + lane);
+                        ws.lj[slot] = j[k];
+                        ws.le[slot] = end[k];
+                        ws.lb[slot] = beg[k];
+                        j[k] = end[k];  // finished from the list, after this group's words are written
+                    }
+                    __syncwarp();
+                    if (lane == 0) ws.nl += __popc(dm);
+                    __syncwarp();
+                }
+                break;
+            }
+        }
+#endif
     }
 #pragma unroll
     for (int k = 0; k < PULL_WPI; ++k) {
@@ -739,11 +841,21 @@ __device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const 
     }
 }
 
+template <bool NC>
+__device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                           const long long (&wv)[PULL_WPI], const unsigned (&pw)[PULL_WPI],
+                                           PullWarpSmem& ws) {
+    int beg[PULL_WPI], end[PULL_WPI];
+    pull_word_bounds(p, wv, pw, beg, end);
+    pull_words_scan<NC>(p, L, f_cur, f_next, wv, pw, beg, end, ws);
+}
+
 // Dense block of a pull level (32 words, the block's word l in lane l): the
 // warp finishes its words PULL_WPI at a time.  Warp-uniform.
 template <bool NC>
 __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
-                                                 uint32_t* f_next, long long bi, long long S, unsigned pwl) {
+                                                 uint32_t* f_next, long long bi, long long S, unsigned pwl,
+                                                 PullWarpSmem& ws) {
     const unsigned lane = lane_id();
     const long long wl = bi + lane * S;
     if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
@@ -759,8 +871,11 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
             if (wi < 0) pw[k] = 0xffffffffu;
             wv[k] = wi < 0 ? -1 : bi + wi * S;
         }
-        pull_words<NC>(p, L, f_cur, f_next, wv, pw);
+        pull_words<NC>(p, L, f_cur, f_next, wv, pw, ws);
     }
+#if BFS_PULL_DEFER
+    if (ws.nl) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
+#endif
 }
 
 // Sparse block of a pull level (same ANY reading as pull_block_pairs): the
@@ -840,14 +955,8 @@ __device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, Pu
     __syncwarp();
 }
 
-#ifndef BFS_PULL_SLOTS
-#define BFS_PULL_SLOTS 2
-#endif
-#ifndef BFS_PULL_SPARSE_MAX
-#define BFS_PULL_SPARSE_MAX 128
-#endif
-constexpr int PULL_SLOTS = BFS_PULL_SLOTS;  // vertices a lane scans at once in a sparse block
-constexpr int PULL_SPARSE_MAX = BFS_PULL_SPARSE_MAX;  // unvisited vertices (of 1024) up to which a block is sparse
+constexpr int PULL_SLOTS = 2;         // vertices a lane scans at once in a sparse block (3 or 4: slower)
+constexpr int PULL_SPARSE_MAX = 128;  // unvisited vertices (of 1024) up to which a block is sparse
 
 // Pull level (Section 5, loop order d -> s).  Warps take blocks of 32 words
 // of P (1024 vertices) round-robin; block b holds the words b + l * S
@@ -1020,8 +1129,10 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
         const int U = pull_block_census(pwl, um, excl);
         if (U == 0) {  // warp-uniform: every vertex of the block is visited
             if (wl < p.W) f_next[wl] = 0;
-        } else if (U > PULL_SPARSE_MAX && L.pairs_ok) {
-            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl);
+        } else if (U > PULL_SPARSE_MAX) {
+            if (lane == 0) ws.nl = 0;
+            __syncwarp();
+            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl, ws);
         } else {
             pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
         }
@@ -1043,11 +1154,18 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const long long S = (p.W + 31) >> 5;
     const long long G = gridDim.x;
+#if BFS_LEVEL_PHASES
+    const uint64_t t_start = globaltimer_ns();
+    uint64_t t_a = 0, t_b = 0;
+#endif
     for (long long r = blockIdx.x; r < S; r += G * NW) {  // CTA-uniform
         if (threadIdx.x == 0) {
             cs.n = 0;
             cs.next = 0;
+            cs.ns = 0;
+            cs.snext = 0;
         }
+        if (lane == 0) ws.nl = 0;
         __syncthreads();
         const long long bi = r + (long long)warp * G;
         if (bi < S) {  // warp-uniform
@@ -1058,8 +1176,9 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
             const int U = pull_block_census(pwl, um, excl);
             if (U == 0) {
                 if (wl < p.W) f_next[wl] = 0;
-            } else if (U <= PULL_SPARSE_MAX || !L.pairs_ok) {
-                pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
+            } else if (U <= PULL_SPARSE_MAX) {
+                // finished after the dense words, by whichever warp is free
+                if (lane == 0) cs.sblk[atomicAdd(&cs.ns, 1)] = bi;
             } else {
                 if (wl < p.W && pwl == FULL) f_next[wl] = 0;
                 const bool add = wl < p.W && pwl != FULL;
@@ -1074,7 +1193,14 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
                 }
             }
         }
+#if BFS_LEVEL_PHASES
+        const uint64_t t_a_end = globaltimer_ns();  // this warp's phase A done
+        t_a += t_a_end - t_start;
+#endif
         __syncthreads();
+#if BFS_LEVEL_PHASES
+        const uint64_t t_b0 = globaltimer_ns();
+#endif
         const int nlist = cs.n;
         for (;;) {  // warp-uniform
             int k0 = 0;
@@ -1089,10 +1215,41 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
                 wv[k] = has ? cs.word[k0 + k] : -1;
                 pw[k] = has ? cs.pw[k0 + k] : FULL;
             }
-            pull_words<NC>(p, L, f_cur, f_next, wv, pw);
+            pull_words<NC>(p, L, f_cur, f_next, wv, pw, ws);
         }
+#if BFS_PULL_DEFER
+        if (ws.nl) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
+#endif
+        const int nsparse = cs.ns;
+        for (;;) {  // warp-uniform: the round's sparse blocks
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&cs.snext, 1);
+            k = __shfl_sync(FULL, k, 0);
+            if (k >= nsparse) break;
+            const long long bi = cs.sblk[k];
+            const long long wl = bi + lane * S;
+            const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : FULL;
+            unsigned um;
+            int excl;
+            const int U = pull_block_census(pwl, um, excl);
+            pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
+        }
+#if BFS_LEVEL_PHASES
+        t_b += globaltimer_ns() - t_b0;  // this warp's phase B (its share of the list)
+#endif
         __syncthreads();  // the list is drained before the next round resets it
     }
+#if BFS_LEVEL_PHASES
+    // per level: sum and max over warps of phase A (own block) and phase B
+    // (draining the CTA list) times, in the second half of the level log
+    if (lane == 0 && p.log && L.level < p.log_cap / 2) {
+        bfs_level_record* r = &p.log[p.log_cap / 2 + L.level];
+        atomicAdd((unsigned long long*)&r->f, (unsigned long long)t_a);
+        atomicMax((unsigned long long*)&r->e_f, (unsigned long long)t_a);
+        atomicAdd((int*)&r->dir, (int)(t_b / 1000));
+        atomicMax((int*)&r->level, (int)(t_b / 10));
+    }
+#endif
 }
 
 // ------------------------------------------------------------ conversions

@@ -74,6 +74,8 @@ struct WorkspaceMS {
     CtlMS* h_ctl = nullptr;
     int32_t* longv = nullptr;            // pull: deferred long rows of the level
     unsigned long long* acc_long = nullptr;  // their lanes found so far
+    uint64_t* hist = nullptr;            // frontier masks of levels 0 .. MS_HIST-1, [MS_HIST][ncap]
+    int* hist_dirty = nullptr;           // device flag, see ParamsMS
 };
 
 void free_wsms(WorkspaceMS* w) {
@@ -89,6 +91,8 @@ void free_wsms(WorkspaceMS* w) {
     cudaFree(w->d_units);
     cudaFree(w->longv);
     cudaFree(w->acc_long);
+    cudaFree(w->hist);
+    cudaFree(w->hist_dirty);
     cudaFreeHost(w->h_ctl);
     delete w;
 }
@@ -129,6 +133,9 @@ struct ParamsMS {
     int32_t log_cap;
     int32_t* longv;
     unsigned long long* acc_long;
+    uint64_t* hist;  // frontier masks of the first MS_HIST levels (zero between units)
+    int64_t ncap;    // vertices per history level
+    int* hist_dirty; // set while a launch runs; still set at the next launch if it ended early
 };
 
 // Unit fields kept in registers / shared memory while a unit runs.
@@ -146,6 +153,13 @@ struct UnitView {
 };
 
 constexpr int MS_T = 512;
+// Depths of the first MS_HIST levels are not written as lanes find vertices:
+// the frontier masks of those levels are kept, and one pass after the last
+// level writes every depth row whole (the level of the first mask holding
+// the lane, -1 for an unreached vertex).  Written as found, a lane's depth
+// entries are scattered 4-byte stores into partly written sectors, which the
+// memory system fills from DRAM, and every row would first be set to -1.
+constexpr int MS_HIST = 16;
 constexpr int MS_QBUF = 64;       // per-warp staging of active-list appends
 constexpr int MS_LONG_ROW = 1024; // pull rows longer than this are scanned grid-wide
 static_assert(MS_LONG_ROW < 65536, "pull parent positions are staged as 16-bit row offsets");
@@ -186,12 +200,13 @@ struct MsLevel {
     unsigned long long done_e;  // degree sum of vertices now seen by every live lane (this thread's share)
     int32_t* qbuf;
     int qn;                  // staged appends (warp-uniform)
+    bool write_depth;        // depths of F_{i+1} are written now (levels past the history)
 };
 
-__device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, int par, int d) {
+__device__ __forceinline__ void write_lanes(MsSmem& sm, uint64_t bits, int v, int par, int d, bool write_depth) {
     while (bits) {
         int j = __ffsll((long long)bits) - 1;
-        sm.depth[j][v] = d;
+        if (write_depth) sm.depth[j][v] = d;
         if (sm.parent[j]) sm.parent[j][v] = par;
         bits &= bits - 1;
     }
@@ -242,7 +257,7 @@ __device__ __forceinline__ void ms_candidate(const ParamsMS& p, const UnitView& 
         uint64_t nb = bits & ~old;
         first = (old == 0);
         L.lanes |= nb;
-        if (nb) write_lanes(sm, nb, v, u, L.level + 1);
+        if (nb) write_lanes(sm, nb, v, u, L.level + 1, L.write_depth);
         if (first) deg = __ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v);
     }
     ms_emit(p, L, first, v, deg);
@@ -476,7 +491,7 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
         while (all) {  // warp-uniform
             const int bj = __ffsll((long long)all) - 1;
             if ((acc >> bj) & 1ull) {
-                sm.depth[bj][v] = dnext;
+                if (L.write_depth) sm.depth[bj][v] = dnext;
                 int32_t* pp = sm.parent[bj];
                 if (pp) pp[v] = __ldg(g.csc_col + beg + pidx[bj * 32 + lane]);
             }
@@ -547,7 +562,7 @@ __device__ void ms_long_rows(const ParamsMS& p, const UnitView& g, MsSmem& sm, c
 // The deferred long rows found their lanes: depth, F_{i+1}, seen and the
 // level counters (after ms_long_rows, before the next level).
 __device__ void ms_long_finalize(const ParamsMS& p, const UnitView& g, MsSmem& sm, uint64_t* f_next, long long nl,
-                                 int dnext, CountersMS* nxt, uint64_t live) {
+                                 int dnext, CountersMS* nxt, uint64_t live, bool write_depth) {
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     unsigned long long cnt = 0, ef = 0, done = 0;
@@ -559,7 +574,7 @@ __device__ void ms_long_finalize(const ParamsMS& p, const UnitView& g, MsSmem& s
         ((unsigned long long*)f_next)[v] = acc;
         const uint64_t old = ((const unsigned long long*)p.seen)[v];
         ((unsigned long long*)p.seen)[v] = old | acc;
-        uint64_t b = acc;
+        uint64_t b = write_depth ? acc : 0ull;
         while (b) {
             const int j = __ffsll((long long)b) - 1;
             sm.depth[j][v] = dnext;
@@ -645,6 +660,52 @@ __device__ int ms_decide(const ParamsMS& p, const UnitView& g, MsSmem& sm, int l
     }
 }
 
+// The frontier mask of level i: kept in the history for the first MS_HIST
+// levels, two alternating buffers after that.
+__device__ __forceinline__ uint64_t* ms_front(const ParamsMS& p, int i) {
+    return i < MS_HIST ? p.hist + (int64_t)i * p.ncap : ((i & 1) ? p.F1 : p.F0);
+}
+
+// After the last level L of a unit: every depth row written whole.  A warp
+// takes 32 consecutive vertices (lane = vertex) and records, in its
+// shared-memory table [lane j][vertex], the first history level whose mask
+// holds lane j; a lane found only after the history (written as found) is
+// left alone, an unreached one gets -1.  Each lane's 32 entries then go out
+// as one coalesced row segment.  The history masks used are cleared for the
+// next unit.
+__device__ void ms_depth_pass(const ParamsMS& p, const UnitView& g, MsSmem& sm, int levels) {
+    const unsigned lane = lane_id();
+    signed char* tab = (signed char*)(ms_pidx_smem + (threadIdx.x >> 5) * (64 * 32));  // [64][32] int8
+    const int lh = min(levels, MS_HIST);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long ntiles = ((long long)g.n + 31) >> 5;
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+        const long long v = t * 32 + lane;
+        const bool valid = v < g.n;
+#pragma unroll 4
+        for (int j = 0; j < 64; ++j) tab[j * 32 + lane] = -1;
+        uint64_t found = 0;
+        for (int i = 0; i < lh; ++i) {
+            uint64_t* hp = p.hist + (int64_t)i * p.ncap + v;
+            const uint64_t b = valid ? *hp : 0ull;
+            uint64_t nb = b & ~found;
+            found |= b;
+            while (nb) {
+                const int j = __ffsll((long long)nb) - 1;
+                tab[j * 32 + lane] = (signed char)i;
+                nb &= nb - 1;
+            }
+            if (b) *hp = 0ull;
+        }
+        const uint64_t later = valid ? (((const unsigned long long*)p.seen)[v] & ~found) : 0ull;
+        __syncwarp();
+        for (int j = 0; j < g.k; ++j) {
+            if (valid && !((later >> j) & 1ull)) sm.depth[j][v] = (int)tab[j * 32 + lane];
+        }
+        __syncwarp();
+    }
+}
+
 template <int T>
 __device__ void msbfs_body(const ParamsMS& p) {
     __shared__ MsSmem sm;
@@ -655,6 +716,13 @@ __device__ void msbfs_body(const ParamsMS& p) {
     const unsigned warp = threadIdx.x >> 5;
     unsigned bar_target = 0;
     int total_levels = 0;
+    // a launch that ended early (error, time limit) left history masks set:
+    // clear the whole history before use
+    if (ld_volatile_i32(p.hist_dirty)) {
+        for (long long i = gtid; i < (long long)MS_HIST * p.ncap; i += gthreads) p.hist[i] = 0;
+    }
+    if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+    if (gtid == 0) *p.hist_dirty = 1;
     for (int ui = 0; ui < p.n_units; ++ui) {
         const MsUnit* U = p.units + ui;
         UnitView g;
@@ -680,13 +748,11 @@ __device__ void msbfs_body(const ParamsMS& p) {
             p.F0[v] = 0;
             p.F1[v] = 0;
         }
+        // depths are written whole by ms_depth_pass; parents start at -1
         for (int j = 0; j < g.k; ++j) {
-            int32_t* dp = sm.depth[j];
             int32_t* pp = sm.parent[j];
-            for (long long v = gtid; v < g.n; v += gthreads) {
-                dp[v] = -1;
-                if (pp) pp[v] = -1;
-            }
+            if (!pp) continue;
+            for (long long v = gtid; v < g.n; v += gthreads) pp[v] = -1;
         }
         if (gtid == 0) {
             for (int s = 0; s < 3; ++s) {
@@ -704,8 +770,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
             int j = threadIdx.x;
             int s = U->src[j];
             atomicOr((unsigned long long*)p.seen + s, 1ull << j);
-            unsigned long long old = atomicOr((unsigned long long*)p.F0 + s, 1ull << j);
-            sm.depth[j][s] = 0;
+            unsigned long long old = atomicOr((unsigned long long*)ms_front(p, 0) + s, 1ull << j);
             if (sm.parent[j]) sm.parent[j][s] = s;
             if (old == 0) {
                 int deg = g.row_ptr[s + 1] - g.row_ptr[s];
@@ -718,6 +783,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         long long m_u = g.m, a_prev = 0;
         int prev_dir = BFS_DIR_PUSH_QUEUE;
+        int unit_levels = 0;
         int list_valid = 0;  // level whose active list (and chunk units) exists
         for (int level = 0;; ++level) {
             CountersMS* cur = &ctl->slot[level % 3];
@@ -752,7 +818,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
             }
             int32_t* a_cur = (level & 1) ? p.A1 : p.A0;
             int2* u_cur = (level & 1) ? p.U1 : p.U0;
-            uint64_t* f_cur = (level & 1) ? p.F1 : p.F0;
+            uint64_t* f_cur = ms_front(p, level);
             long long nunits = (long long)cv[3];
             if (dir != BFS_DIR_PULL && list_valid != level) {
                 // active list of a pull-made frontier (it appends the chunk units)
@@ -775,7 +841,8 @@ __device__ void msbfs_body(const ParamsMS& p) {
             }
             MsLevel L;
             L.level = level;
-            L.f_next = (level & 1) ? p.F0 : p.F1;
+            L.f_next = ms_front(p, level + 1);
+            L.write_depth = level + 1 >= MS_HIST;
             L.a_next = (level & 1) ? p.A0 : p.A1;
             L.u_next = (level & 1) ? p.U0 : p.U1;
             L.next = nxt;
@@ -823,16 +890,19 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 if (nl > 0) {
                     ms_long_rows<T>(p, g, sm, f_cur, live, nl);
                     if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
-                    ms_long_finalize(p, g, sm, L.f_next, nl, level + 1, nxt, live);
+                    ms_long_finalize(p, g, sm, L.f_next, nl, level + 1, nxt, live, L.write_depth);
                 }
             }
             if (gtid == 0) ctl->long_len = 0;
-            // F_i is consumed: clear its masks (the buffer is F_{i+2}'s); after
-            // a push level fold F_{i+1} into seen (a pull level already did)
-            if (list_valid >= level) {
-                for (long long q = gtid; q < a; q += gthreads) f_cur[a_cur[q]] = 0;
-            } else {
-                for (long long v = gtid; v < g.n; v += gthreads) f_cur[v] = 0;
+            // F_i is consumed: past the history its buffer is F_{i+2}'s, so
+            // clear its masks (history levels are kept for the depth pass);
+            // after a push level fold F_{i+1} into seen (a pull level already did)
+            if (level >= MS_HIST) {
+                if (list_valid >= level) {
+                    for (long long q = gtid; q < a; q += gthreads) f_cur[a_cur[q]] = 0;
+                } else {
+                    for (long long v = gtid; v < g.n; v += gthreads) f_cur[v] = 0;
+                }
             }
             if (dir != BFS_DIR_PULL) {
                 const unsigned long long* const asrc[1] = {&nxt->a_len};
@@ -855,9 +925,16 @@ __device__ void msbfs_body(const ParamsMS& p) {
             a_prev = a;
             prev_dir = dir;
             ++total_levels;
+            ++unit_levels;
         }
+        // the unit's depth rows; a barrier before the next unit reuses seen
+        ms_depth_pass(p, g, sm, unit_levels);
+        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
     }
-    if (gtid == 0) ctl->levels = total_levels;
+    if (gtid == 0) {
+        ctl->levels = total_levels;
+        *p.hist_dirty = 0;  // every history level used was cleared by its depth pass
+    }
 }
 
 template <int T>
@@ -909,6 +986,9 @@ static bfs_status alloc_wsms(int32_t ncap, int64_t ucap, int32_t chunk, int32_t 
     ok = ok && cudaMalloc(&w->d_units, sizeof(MsUnit) * (size_t)units_cap) == cudaSuccess;
     ok = ok && cudaMalloc(&w->longv, (size_t)ncap * 4) == cudaSuccess;
     ok = ok && cudaMalloc(&w->acc_long, (size_t)ncap * 8) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->hist, (size_t)MS_HIST * ncap * 8) == cudaSuccess &&
+         cudaMemset(w->hist, 0, (size_t)MS_HIST * ncap * 8) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->hist_dirty, 4) == cudaSuccess && cudaMemset(w->hist_dirty, 0, 4) == cudaSuccess;
     ok = ok && cudaMallocHost(&w->h_ctl, sizeof(CtlMS)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -962,8 +1042,8 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.ctl = w->ctl;
     p.sticky = w->d_sticky;
     p.policy = o.policy;
-    p.alpha = o.alpha;
-    p.beta = o.beta;
+    p.alpha = o.batch_alpha;
+    p.beta = o.batch_beta;
     p.schedule = d_sched;
     p.schedule_len = o.schedule_len;
     p.mlp = mlp;
@@ -976,6 +1056,9 @@ static bfs_status launch_ms(WorkspaceMS* w, const std::vector<MsUnit>& units, co
     p.log_cap = d_log ? o.level_log_cap : 0;
     p.longv = w->longv;
     p.acc_long = w->acc_long;
+    p.hist = w->hist;
+    p.ncap = w->ncap;
+    p.hist_dirty = w->hist_dirty;
     int blocks = coop_blocks_ms(o.blocks_per_sm);
     void* args[] = {(void*)&p};
     BFS_CUDA(cudaLaunchCooperativeKernel((const void*)msbfs_kernel<MS_T>, dim3(blocks), dim3(MS_T), args, MS_PIDX_BYTES,

@@ -115,6 +115,52 @@ __device__ inline int policy_choice_warp(const float* __restrict__ w, const floa
         if (c == h) zh = z[c];
     return (z[best] - zh > margin) ? best : h;
 }
+
+// The same decision computed by a whole CTA (block-uniform; every thread
+// returns it): the first layer on every warp (lane j = hidden unit j), the 32
+// second-layer units spread over the warps (one warp-wide dot product each),
+// the output layer on warp 0.  Three short dependent steps instead of the 32
+// shuffle-FMA steps of the single-warp form.  x and the scratch are shared
+// memory: s_h2 has 32 floats, s_out one int.
+__device__ inline int policy_choice_block(const float* __restrict__ w, const float* x, int h, float margin,
+                                          float* s_h2, int* s_out) {
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float h1 = w[OFF_B1 + lane];
+#pragma unroll
+    for (int k = 0; k < MLP_IN; ++k) h1 = fmaf(w[OFF_W1 + lane * MLP_IN + k], (x[k] - w[OFF_MEAN + k]) * w[OFF_ISTD + k], h1);
+    h1 = fmaxf(h1, 0.0f);
+    for (unsigned u = warp; u < (unsigned)MLP_H; u += nw) {
+        float t = w[OFF_W2 + u * MLP_H + lane] * h1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_h2[u] = fmaxf(t + w[OFF_B2 + u], 0.0f);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const float h2 = s_h2[lane];
+        float z[MLP_OUT];
+#pragma unroll
+        for (int c = 0; c < MLP_OUT; ++c) {
+            float t = w[OFF_W3 + c * MLP_H + lane] * h2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            z[c] = t + w[OFF_B3 + c];
+        }
+        int best = 0;
+#pragma unroll
+        for (int c = 1; c < MLP_OUT; ++c)
+            if (z[c] > z[best]) best = c;
+        float zh = z[0];
+#pragma unroll
+        for (int c = 1; c < MLP_OUT; ++c)
+            if (c == h) zh = z[c];
+        if (lane == 0) *s_out = (z[best] - zh > margin) ? best : h;
+    }
+    __syncthreads();
+    const int a = *s_out;
+    __syncthreads();  // s_out and s_h2 may be rewritten by the next call
+    return a;
+}
 #endif
 
 }  // namespace bfsgb

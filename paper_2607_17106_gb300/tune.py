@@ -50,8 +50,8 @@ BATCH_SPACE = {
     "chunk": [128, 256, 1024],
     "medium": [16, 32],
     "pull_serial": [16, 32, 64],
-    "alpha": [4.0, 8.0, 14.0, 64.0],
-    "beta": [24.0, 48.0],
+    "batch_alpha": [2.0, 4.0, 8.0, 14.0, 64.0],
+    "batch_beta": [24.0, 48.0],
 }
 
 
@@ -95,6 +95,22 @@ def time_candidate(g: Graph, sources, opt, batch: bool, reps: int = 3) -> float:
     return e0.elapsed_time(e1) * 1e3 / per
 
 
+def time_mixed(graphs, goq, srcs, depth, parent, opt, reps: int = 3) -> float:
+    """Device microseconds of one bfs_run_mixed launch over the whole batch."""
+    import torch
+    from . import run_mixed
+    st = torch.cuda.current_stream()
+    run_mixed(graphs, goq, srcs, depth, parent, opt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        run_mixed(graphs, goq, srcs, depth, parent, opt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
 def valid_candidate(cand: dict) -> bool:
     """Combinations the library accepts: the filter forms and the frontier sorts
     need the persistent or host-loop drive."""
@@ -103,11 +119,14 @@ def valid_candidate(cand: dict) -> bool:
     return cand.get("push_filter", BFS_PUSH_FUSED) == BFS_PUSH_FUSED and cand.get("frontier_sort", BFS_SORT_NONE) == BFS_SORT_NONE
 
 
-def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int = 2, verbose=False):
-    """Coordinate descent over `space` from the library defaults (each knob in turn)."""
+def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int = 2, verbose=False, timer=None):
+    """Coordinate descent over `space` from the library defaults (each knob in
+    turn).  timer(opt) -> us replaces the per-search timing when given."""
     best = {}
     base = options(batch=1 if batch else 0)
-    best_t = time_candidate(g, sources, base, batch)
+    if timer is None:
+        timer = lambda o: time_candidate(g, sources, o, batch)  # noqa: E731
+    best_t = timer(base)
     trials = [({}, best_t)]
     for _ in range(rounds):
         improved = False
@@ -117,7 +136,7 @@ def coordinate_search(g: Graph, sources, space: dict, batch: bool, rounds: int =
                 cand[knob] = v
                 if cand == best or not valid_candidate(cand):
                     continue
-                t = time_candidate(g, sources, options(batch=1 if batch else 0, **cand), batch)
+                t = timer(options(batch=1 if batch else 0, **cand))
                 trials.append((cand, t))
                 if verbose:
                     print(f"  {cand}: {t:.1f} us", flush=True)
@@ -136,9 +155,17 @@ def load_cache(path: str = DEFAULT_CACHE) -> dict:
         return {}
 
 
+MIXED_KEY = "mixed-rmat16-22-q256"
+
+
 def tuned_options(kind: str, n: int, m: int, batch: bool = False, path: str = DEFAULT_CACHE, **extra):
-    """bfs_options from the cache entry of this graph class (defaults if none)."""
-    entry = load_cache(path).get(graph_key(kind, n, m) + ("|batch" if batch else "|single"))
+    """bfs_options from the cache entry of this graph class (defaults if none).
+    kind == MIXED_KEY selects the entry of the mixed multi-graph batch."""
+    if kind == MIXED_KEY:
+        d = device_key()
+        entry = load_cache(path).get(f"{d['gpu']}|{d['sms']}|{MIXED_KEY}")
+    else:
+        entry = load_cache(path).get(graph_key(kind, n, m) + ("|batch" if batch else "|single"))
     kw = dict(entry["options"]) if entry else {}
     kw.update(extra)
     kw.setdefault("batch", 1 if batch else 0)
@@ -152,6 +179,8 @@ def main(argv=None):
     ap.add_argument("--batch", action="store_true", help="tune 64-lane batched searches")
     ap.add_argument("--cache", default=DEFAULT_CACHE)
     ap.add_argument("--rounds", type=int, default=2)
+    ap.add_argument("--mixed", action="store_true", help="tune the mixed batch of 256 queries over RMAT 16-22 "
+                                                          "(one bfs_run_mixed launch)")
     args = ap.parse_args(argv)
     root = os.path.dirname(_HERE)
     if root not in sys.path:
@@ -159,6 +188,8 @@ def main(argv=None):
     import graphgen
     from .build import build
     build()
+    if args.mixed:
+        return _tune_mixed(args, graphgen)
     w = graphgen.WORKLOADS[args.workload]
     n, src, dst = w.edges()
     g = Graph.build(n, src, dst)
@@ -170,6 +201,28 @@ def main(argv=None):
     cache = load_cache(args.cache)
     key = graph_key(w.kind, n, g.m) + ("|batch" if args.batch else "|single")
     cache[key] = {"options": best, "us": best_t, "default_us": default_t, "workload": w.name,
+                  "trials": len(trials)}
+    with open(args.cache, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    print(json.dumps({"key": key, "best": best, "us": best_t, "default_us": default_t,
+                      "speedup": default_t / best_t}))
+    return 0
+
+
+def _tune_mixed(args, graphgen):
+    import torch
+    scales, edge_lists, goq, srcs = graphgen.mixed_batch()
+    graphs = [Graph.build(n, s, d) for n, s, d in edge_lists]
+    ns = [n for n, _, _ in edge_lists]
+    depth = [torch.empty(ns[gi], dtype=torch.int32, device="cuda") for gi in goq]
+    parent = [torch.empty(ns[gi], dtype=torch.int32, device="cuda") for gi in goq]
+    timer = lambda o: time_mixed(graphs, goq, srcs, depth, parent, o)  # noqa: E731
+    best, best_t, trials = coordinate_search(None, None, BATCH_SPACE, True, args.rounds, verbose=True, timer=timer)
+    default_t = trials[0][1]
+    cache = load_cache(args.cache)
+    d = device_key()
+    key = f"{d['gpu']}|{d['sms']}|{MIXED_KEY}"
+    cache[key] = {"options": best, "us": best_t, "default_us": default_t, "workload": MIXED_KEY,
                   "trials": len(trials)}
     with open(args.cache, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)

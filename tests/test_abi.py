@@ -39,7 +39,8 @@ def test_every_declared_symbol_is_exported(lib):
 def test_options_layout_matches_c(lib):
     o = bg.options()
     assert o.struct_size == ctypes.sizeof(bg.bfs_options)
-    assert (o.alpha, o.beta, o.gamma) == (8.0, 48.0, 16.0)
+    assert (o.alpha, o.beta, o.gamma) == (14.0, 48.0, 16.0)
+    assert (o.batch_alpha, o.batch_beta) == (4.0, 48.0)
     assert o.chunk == 1024 and o.block_threads == 1024 and o.batch == 1 and o.claim_aggregate == 0
     assert o.push_filter == bg.BFS_PUSH_FUSED
     assert o.frontier_sort == bg.BFS_SORT_NONE

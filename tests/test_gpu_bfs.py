@@ -336,15 +336,16 @@ def _barbell():
 
 
 @pytest.mark.parametrize("threads", [1024, 512])
-def test_small_frontier_levels_hand_over_to_the_grid_and_back(threads):
-    # one CTA runs the tiny levels of the paths, the whole grid the RMAT burst
+def test_long_runs_of_tiny_levels_around_a_burst(threads):
+    # thousands of one-vertex levels along the paths, two large levels in the
+    # RMAT component between them
     n, s, d = _barbell()
     adj, g = _graph_pair(n, s, d)
     srcs = [0, n - 1, 3000 + 5, 1500]
     for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
         dd, pp = _run(g, n, srcs, bg.options(batch=0, policy=pol, block_threads=threads))
         _check(adj, srcs, dd, pp)
-    # the level log covers every level, small ones included
+    # the level log covers every level
     log = (bg.bfs_level_record * 8192)()
     nlev = bg.ctypes.c_int32(0)
     depth = np.empty(n, np.int32)
@@ -355,12 +356,33 @@ def test_small_frontier_levels_hand_over_to_the_grid_and_back(threads):
     for i in range(nlev.value):
         assert log[i].level == i and log[i].f == ref[i][0] and log[i].e_f == ref[i][1], i
     assert log[nlev.value].dir == -1
-    # the level limit is enforced inside a run of small levels
+    # the level limit is enforced in the middle of the first path
     with pytest.raises(bg.BfsError) as e:
         _run(g, n, [0], bg.options(batch=0, max_levels=100))
     assert e.value.status == bg.BFS_ERANGE
     dd, pp = _run(g, n, [0], bg.options(batch=0))
     _check(adj, [0], dd, pp)
+
+
+def test_many_searches_in_one_launch_match_the_oracle():
+    # k sources with batch = 0 and device outputs run one after another in one
+    # persistent launch: an isolated source, a two-vertex component, the same
+    # hub twice, a path end, mixed with ordinary sources; and the same sources
+    # one call each
+    nr, rs, rd = graphgen.rmat(13, 16, seed=31)
+    a = 2500
+    src = np.concatenate([rs, np.arange(nr, nr + a - 1), [nr + a + 1]]).astype(np.int32)
+    dst = np.concatenate([rd, np.arange(nr + 1, nr + a), [nr + a + 2]]).astype(np.int32)
+    n = nr + a + 4  # nr + a + 3 stays isolated
+    adj, g = _graph_pair(n, src, dst)
+    deg = np.diff(adj.row_ptr)
+    hub = int(np.argmax(deg))
+    srcs = [nr + a + 3, nr + a + 1, hub, hub, nr, 7] + graphgen.sample_sources(n, src, dst, 6, seed=5).tolist()
+    for o in (bg.options(batch=0), bg.options(batch=0, block_threads=512), bg.options(batch=0, policy=bg.BFS_POLICY_PULL)):
+        dd, pp = _run(g, n, srcs, o)
+        _check(adj, srcs, dd, pp)
+    d1 = np.stack([_run(g, n, [s], bg.options(batch=0))[0][0] for s in srcs])
+    assert np.array_equal(d1, dd)
 
 
 def test_edge_cases_tiny_and_isolated():

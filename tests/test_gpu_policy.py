@@ -218,13 +218,22 @@ def test_policy_pipeline_trains_and_drives_searches():
     pol_ce = pl.fit(X, y, epochs=300, lr=3e-3)
     assert np.isfinite(pol_ce.final_loss)
     assert pl.predict(pol_ce, X).shape == y.shape
-    # the log-time regression: on the levels it was trained on, the
-    # network's choices cost no more time than the heuristic's (K)
     pol = pl.fit(X, None, epochs=600, lr=3e-3, target=pl.log_time_targets(T))
     choice = pl.predict(pol, X)
     assert choice.shape == y.shape
-    r_mlp, r_heur = pl.regret(pl.gate(pl.outputs(pol, X), X, K), T), pl.regret(K, T)
-    assert r_mlp["time_us"] <= r_heur["time_us"] * 1.02, (r_mlp, r_heur)
+    # held-out levels (other families and seeds than the training specs): the
+    # gated network's choices, timed form by form from the heuristic's own
+    # level states, cost no more than the heuristic's choices beyond timing
+    # noise.  This is a safety property, not a gain: on these families the
+    # heuristic is within about 1 % of the best form at every level, and the
+    # measured end-to-end effect of the policy is a small loss (see the
+    # policy report)
+    held = [dict(kind="rmat", scale=14, a=0.62, b=0.165, c=0.165, edge_factor=24, seed=991),
+            dict(kind="er", n=1 << 14, m_pairs=12 << 14, seed=992),
+            dict(kind="grid", width=160, height=120, p_del=0.15, seed=993)]
+    Xh, Th, Kh, _ = pl.collect(held, sources_per_graph=2, repeats=3)
+    r_mlp, r_heur = pl.regret(pl.gate(pl.outputs(pol, Xh), Xh, Kh), Th), pl.regret(Kh, Th)
+    assert r_mlp["time_us"] <= r_heur["time_us"] * 1.01, (r_mlp, r_heur)
     import graphgen
     n, s, d = graphgen.rmat(13, 16, seed=5)
     adj = oracle.build_adjacency(n, s, d)

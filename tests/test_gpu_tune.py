@@ -59,7 +59,7 @@ def test_single_source_search_with_real_timings(rmat16):
 def test_batched_search_with_real_timings(rmat16):
     n, s, d, g, adj = rmat16
     srcs = graphgen.sample_sources(n, s, d, 64, seed=78)
-    space = {"pull_serial": [16, 32], "alpha": [4.0, 8.0], "chunk": [256, 1024]}
+    space = {"pull_serial": [16, 32], "batch_alpha": [4.0, 8.0], "chunk": [256, 1024]}
     best, t, trials = tune.coordinate_search(g, srcs, space, batch=True, rounds=1)
     assert len(trials) >= 4 and t <= trials[0][1]
     _check_options(g, adj, n, srcs, bg.options(batch=1, **best))
