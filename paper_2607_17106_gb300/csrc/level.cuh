@@ -634,79 +634,11 @@ __device__ __forceinline__ void pull_word_bounds(const Params1& p, const long lo
     }
 }
 
-#ifndef BFS_PULL_DEFER
-#define BFS_PULL_DEFER 0
-#endif
-// Dense pull words: after 2, 4 or 8 entries, when few of a group's vertices
-// are still scanning, those rows leave the group for the warp's leftover
-// list, so the longest scans no longer hold 64 lanes; the list is finished
-// lane-per-row when full and at the end.
-// checkpoint k (after 2, 4, 8 entries) defers when at most 16, 24, 32 lanes are open
-__device__ __forceinline__ int pull_defer_max(int entries) {
-    return entries == 2 ? 16 : entries == 4 ? 24 : entries == 8 ? 32 : -1;
-}
-
-// The warp's leftover rows (ws.lv: vertex, lj: next entry, le: end, lb: row
-// start; at most 32): lane l scans row l four entries a step (first hit in
-// row order is the parent), then rows still open are finished one at a time
-// by the whole warp.  Found vertices set their bits in F_{i+1} and P with
-// atomics: the words' plain stores by their group came first.  Warp-uniform.
-template <bool NC>
-__device__ __noinline__ void pull_leftovers(const Params1& p, LevelCtx& L, PullWarpSmem& ws, const uint32_t* f_cur,
-                                            uint32_t* f_next) {
-    constexpr unsigned FULL = 0xffffffffu;
-    __syncwarp();
-    const int nl = min(ws.nl, 32);
-    const unsigned lane = lane_id();
-    const bool has = (int)lane < nl;
-    const int v = has ? ws.lv[lane] : 0, b = has ? ws.lb[lane] : 0, e = has ? ws.le[lane] : 0;
-    int j = has ? ws.lj[lane] : 0;
-    int hit = -1;
-    for (int step = 0; step < 8 && __any_sync(FULL, has && hit < 0 && j < e); ++step) {
-        int uu[4];
-        unsigned fw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) uu[q] = (has && hit < 0 && j + q < e) ? __ldg(p.csc_col + j + q) : -1;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fw[q] = uu[q] >= 0 ? ld_word<NC>(f_cur, uu[q] >> 5) : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (hit < 0 && uu[q] >= 0 && ((fw[q] >> (uu[q] & 31)) & 1u)) hit = uu[q];
-        if (hit < 0) j += 4;
-    }
-    unsigned rm = __ballot_sync(FULL, has && hit < 0 && j < e);
-    while (rm) {
-        const int l = __ffs(rm) - 1;
-        const int bl = __shfl_sync(FULL, j, l), el = __shfl_sync(FULL, e, l);
-        int h = -1;
-        for (int base = bl; base < el && h < 0; base += 32) {
-            const int idx = base + (int)lane;
-            const int uu = idx < el ? __ldg(p.csc_col + idx) : -1;
-            const bool t = uu >= 0 && ((ld_word<NC>(f_cur, uu >> 5) >> (uu & 31)) & 1u);
-            const unsigned hb = __ballot_sync(FULL, t);
-            if (hb) h = __shfl_sync(FULL, uu, __ffs(hb) - 1);
-        }
-        if ((int)lane == l) hit = h;
-        rm &= rm - 1;
-    }
-    if (has && hit >= 0) {
-        L.depth[v] = L.level + 1;
-        if (L.parent) L.parent[v] = hit;
-        L.ef += (unsigned long long)(p.symmetric ? (e - b) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
-        L.cnt += 1;
-        atomicOr(f_next + (v >> 5), 1u << (v & 31));
-        atomicOr(p.P + (v >> 5), 1u << (v & 31));
-    }
-    __syncwarp();
-    if (lane == 0) ws.nl = 0;
-    __syncwarp();
-}
-
 template <bool NC>
 __device__ __forceinline__ void pull_words_scan(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
                                                 uint32_t* f_next, const long long (&wv)[PULL_WPI],
                                                 const unsigned (&pw)[PULL_WPI], const int (&beg)[PULL_WPI],
-                                                const int (&end)[PULL_WPI], PullWarpSmem& ws) {
+                                                const int (&end)[PULL_WPI]) {
     const unsigned lane = lane_id();
     const int dnext = L.level + 1;
     const int serial = min(p.pull_serial, PULL_SERIAL_MAX);
@@ -733,12 +665,7 @@ __device__ __forceinline__ void pull_words_scan(const Params1& p, LevelCtx& L, c
                 u[k][r] = (lk && j[k] + r < end[k]) ? __ldg(p.csc_col + j[k] + r) : -1;
             live |= lk;
         }
-#if BFS_PULL_DEFER
-        // the deferral below is warp-synchronous: the loop ends for all lanes together
-        if (!__any_sync(0xffffffffu, live)) break;
-#else
         if (!live) break;
-#endif
 #pragma unroll
         for (int k = 0; k < PULL_WPI; ++k)
 #pragma unroll
@@ -758,38 +685,6 @@ __device__ __forceinline__ void pull_words_scan(const Params1& p, LevelCtx& L, c
                 j[k] += PULL_R;
             }
         }
-#if BFS_PULL_DEFER
-        const int dmax = pull_defer_max(step + PULL_R);
-        if (dmax > 0) {
-            int open = 0;
-#pragma unroll
-            for (int k = 0; k < PULL_WPI; ++k) open += __popc(__ballot_sync(0xffffffffu, !found[k] && j[k] < end[k]));
-            if (open > 0 && open <= dmax) {  // warp-uniform
-                // make room first, finishing rows of earlier groups only: this
-                // group's words are written after the loop, and a row of its
-                // own finished before that would have its bits overwritten
-                if (ws.nl + open > 32) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
-#pragma unroll
-                for (int k = 0; k < PULL_WPI; ++k) {
-                    const bool d = !found[k] && j[k] < end[k];
-                    const unsigned dm = __ballot_sync(0xffffffffu, d);
-                    if (!dm) continue;
-                    if (d) {
-                        const int slot = ws.nl + __popc(dm & lanemask_lt());
-                        ws.lv[slot] = (int)(wv[k] * 32 + lane);
-                        ws.lj[slot] = j[k];
-                        ws.le[slot] = end[k];
-                        ws.lb[slot] = beg[k];
-                        j[k] = end[k];  // finished from the list, after this group's words are written
-                    }
-                    __syncwarp();
-                    if (lane == 0) ws.nl += __popc(dm);
-                    __syncwarp();
-                }
-                break;
-            }
-        }
-#endif
     }
 #pragma unroll
     for (int k = 0; k < PULL_WPI; ++k) {
@@ -843,19 +738,17 @@ __device__ __forceinline__ void pull_words_scan(const Params1& p, LevelCtx& L, c
 
 template <bool NC>
 __device__ __forceinline__ void pull_words(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                                           const long long (&wv)[PULL_WPI], const unsigned (&pw)[PULL_WPI],
-                                           PullWarpSmem& ws) {
+                                           const long long (&wv)[PULL_WPI], const unsigned (&pw)[PULL_WPI]) {
     int beg[PULL_WPI], end[PULL_WPI];
     pull_word_bounds(p, wv, pw, beg, end);
-    pull_words_scan<NC>(p, L, f_cur, f_next, wv, pw, beg, end, ws);
+    pull_words_scan<NC>(p, L, f_cur, f_next, wv, pw, beg, end);
 }
 
 // Dense block of a pull level (32 words, the block's word l in lane l): the
 // warp finishes its words PULL_WPI at a time.  Warp-uniform.
 template <bool NC>
 __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, const uint32_t* f_cur,
-                                                 uint32_t* f_next, long long bi, long long S, unsigned pwl,
-                                                 PullWarpSmem& ws) {
+                                                 uint32_t* f_next, long long bi, long long S, unsigned pwl) {
     const unsigned lane = lane_id();
     const long long wl = bi + lane * S;
     if (wl < p.W && pwl == 0xffffffffu) f_next[wl] = 0;
@@ -871,11 +764,8 @@ __device__ __forceinline__ void pull_block_pairs(const Params1& p, LevelCtx& L, 
             if (wi < 0) pw[k] = 0xffffffffu;
             wv[k] = wi < 0 ? -1 : bi + wi * S;
         }
-        pull_words<NC>(p, L, f_cur, f_next, wv, pw, ws);
+        pull_words<NC>(p, L, f_cur, f_next, wv, pw);
     }
-#if BFS_PULL_DEFER
-    if (ws.nl) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
-#endif
 }
 
 // Sparse block of a pull level (same ANY reading as pull_block_pairs): the
@@ -1130,9 +1020,7 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
         if (U == 0) {  // warp-uniform: every vertex of the block is visited
             if (wl < p.W) f_next[wl] = 0;
         } else if (U > PULL_SPARSE_MAX) {
-            if (lane == 0) ws.nl = 0;
-            __syncwarp();
-            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl, ws);
+            pull_block_pairs<NC>(p, L, f_cur, f_next, bi, S, pwl);
         } else {
             pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
         }
@@ -1165,7 +1053,6 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
             cs.ns = 0;
             cs.snext = 0;
         }
-        if (lane == 0) ws.nl = 0;
         __syncthreads();
         const long long bi = r + (long long)warp * G;
         if (bi < S) {  // warp-uniform
@@ -1215,11 +1102,8 @@ __device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_
                 wv[k] = has ? cs.word[k0 + k] : -1;
                 pw[k] = has ? cs.pw[k0 + k] : FULL;
             }
-            pull_words<NC>(p, L, f_cur, f_next, wv, pw, ws);
+            pull_words<NC>(p, L, f_cur, f_next, wv, pw);
         }
-#if BFS_PULL_DEFER
-        if (ws.nl) pull_leftovers<NC>(p, L, ws, f_cur, f_next);
-#endif
         const int nsparse = cs.ns;
         for (;;) {  // warp-uniform: the round's sparse blocks
             int k = 0;
