@@ -68,10 +68,31 @@ void free_ws1(Workspace1* w) {
 
 
 // ------------------------------------------------------------ the kernel
-// Dynamic shared memory of the persistent kernel: a copy of the policy
+// Dynamic shared memory of the persistent kernel: the round list of the
+// list-driven pull (T * 32 16-bit entries), then a copy of the policy
 // weights, evaluated by every CTA at every level when the policy is the MLP.
-constexpr size_t BFS1_DYN_SMEM = (size_t)NWEIGHTS * sizeof(float);
-extern __shared__ float bfs1_dyn_smem[];
+template <int T>
+constexpr size_t bfs1_list_bytes() {
+    return (size_t)T * 32 * sizeof(uint16_t);
+}
+template <int T>
+constexpr size_t bfs1_dyn_smem() {
+    return bfs1_list_bytes<T>() + (size_t)NWEIGHTS * sizeof(float);
+}
+extern __shared__ __align__(16) unsigned char bfs1_dyn[];
+
+// a[0, len) = -1 by the whole grid: 16-byte stores from the first 16-byte
+// boundary, 4-byte stores for the head and the tail.  a is 4-byte aligned.
+__device__ __forceinline__ void fill_minus1(int32_t* a, long long len, long long gtid, long long gthreads) {
+    long long head = (long long)((16u - ((unsigned)(uintptr_t)a & 15u)) & 15u) >> 2;
+    if (head > len) head = len;
+    if (gtid < head) a[gtid] = -1;
+    const long long nv = (len - head) >> 2;
+    int4* const a4 = reinterpret_cast<int4*>(a + head);
+    for (long long i = gtid; i < nv; i += gthreads) a4[i] = make_int4(-1, -1, -1, -1);
+    const long long t0 = head + nv * 4;
+    if (gtid < len - t0) a[t0 + gtid] = -1;
+}
 
 // SORT: the frontier-sort variants are compiled in (a separate instantiation,
 // so that the default kernel carries none of their registers).
@@ -82,9 +103,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ float s_mlp_out;
     const float* mlp_w = nullptr;
     if (p.policy == BFS_POLICY_MLP && p.mlp) {
-        for (int i = threadIdx.x; i < NWEIGHTS; i += T) bfs1_dyn_smem[i] = __ldg(p.mlp + i);
+        float* w = reinterpret_cast<float*>(bfs1_dyn + bfs1_list_bytes<T>());
+        for (int i = threadIdx.x; i < NWEIGHTS; i += T) w[i] = __ldg(p.mlp + i);
         __syncthreads();
-        mlp_w = bfs1_dyn_smem;
+        mlp_w = w;
     }
     Ctl1* ctl = p.ctl;
     const unsigned nblocks = gridDim.x;
@@ -98,6 +120,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     int level = 0, prev_dir = BFS_DIR_PUSH_QUEUE, bm_valid = -1, q_valid = 0;
     long long m_u = 0, f_prev = 0;
     bool done = false;
+    // the -1 rows of the next search of this launch were stored during the
+    // current one (grid-uniform: every CTA takes the same directions)
+    bool prefilled = false, prefill_next = false;
     for (int si = 0; si < nsearch; ++si) {
     int32_t* const depth = p.depth + (int64_t)si * p.n;
     int32_t* const parent = p.parent ? p.parent + (int64_t)si * p.n : nullptr;
@@ -109,10 +134,11 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (w == p.W - 1 && (p.n & 31)) bits |= ~((1u << (p.n & 31)) - 1u);  // phantom vertices
             p.P[w] = bits;
         }
-        for (long long v = gtid; v < p.n; v += gthreads) {
-            depth[v] = (v == s) ? 0 : -1;
-            if (parent) parent[v] = (v == s) ? s : -1;
+        if (!prefilled) {
+            fill_minus1(depth, p.n, gtid, gthreads);
+            if (parent) fill_minus1(parent, p.n, gtid, gthreads);
         }
+        prefilled = false;
         if (gtid == 0) {
             const int rb = __ldg(p.row_ptr + s), re = __ldg(p.row_ptr + s + 1);
             const int deg = re - rb;
@@ -140,6 +166,11 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             ctl->f_prev = 0;
         }
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+        // after the barrier: ordered after every -1 store of the rows
+        if (gtid == 0) {
+            depth[s] = 0;
+            if (parent) parent[s] = s;
+        }
     }
 
     level = __ldcg(&ctl->next_level);
@@ -152,13 +183,22 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     const int level_end = level + p.level_count;
     const unsigned warp = threadIdx.x >> 5;
 
+    // counters of the level about to start (|F_i|, chunk units, e_f), read
+    // by thread 0 right after the level barrier opens (s_cnt_ok), else here
+    __shared__ unsigned long long s_cnt[3];
+    bool s_cnt_ok = false;
     while (!done && level < level_end) {
         Counters* cur = &ctl->slot[level % 3];
         Counters* nxt = &ctl->slot[(level + 1) % 3];
         int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
-        const unsigned long long* const csrc[3] = {&cur->q_len, &cur->u_len, &cur->e_f};
         unsigned long long cv[3];
-        cta_load_u64<3>(csrc, cv);
+        if (s_cnt_ok) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) cv[i] = s_cnt[i];
+        } else {
+            const unsigned long long* const csrc[3] = {&cur->q_len, &cur->u_len, &cur->e_f};
+            cta_load_u64<3>(csrc, cv);
+        }
         long long f = (long long)cv[0];
         long long nunits = (long long)cv[1];
         long long e_f = (long long)cv[2];
@@ -257,7 +297,17 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.err = &p.ctl->bar.err;
         L.precheck = push_precheck(m_u, p.m, e_f);
         if (dir == BFS_DIR_PULL) {
-            pull_level_cta<false, T>(p, L, f_cur, f_nxt, sm.pull.w[warp], sm.pull.c);
+#ifndef BFS_PREFILL
+#define BFS_PREFILL 1
+#endif
+            if (BFS_PREFILL && !prefill_next && p.do_init && si + 1 < nsearch) {
+                // the first pull level of a search is long and latency-bound:
+                // the next search's -1 rows are stored beside its scans
+                fill_minus1(p.depth + (int64_t)(si + 1) * p.n, p.n, gtid, gthreads);
+                if (p.parent) fill_minus1(p.parent + (int64_t)(si + 1) * p.n, p.n, gtid, gthreads);
+                prefill_next = true;
+            }
+            pull_level_list<false, T>(p, L, f_cur, f_nxt, sm.list, reinterpret_cast<uint16_t*>(bfs1_dyn));
         } else {
             push_level<T, SORT>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
             if (p.push_filter != BFS_PUSH_FUSED) {
@@ -297,14 +347,23 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (p.log && done_level < p.log_cap / 2)
                 atomicMax((unsigned long long*)&p.log[p.log_cap / 2 + done_level].t_ns, (unsigned long long)globaltimer_ns());
 #endif
+        }, [&]() {
+            s_cnt[0] = ld_cg_u64(&nxt->q_len);
+            s_cnt[1] = ld_cg_u64(&nxt->u_len);
+            s_cnt[2] = ld_cg_u64(&nxt->e_f);
         });
         if (!ok) return;
+        // the next iteration reads them before any CTA can change them: the
+        // slot is zeroed two levels later
+        s_cnt_ok = true;
 #if BFS_LEVEL_PHASES
         if (gtid == 0 && p.log && done_level < p.log_cap / 2) p.log[p.log_cap / 2 + done_level].m_u = (int64_t)globaltimer_ns();
 #else
         (void)done_level;
 #endif
     }
+    prefilled = prefill_next;
+    prefill_next = false;
     // every CTA is past this search's last level before the next one starts
     if (si + 1 < nsearch && !grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
     }  // searches
@@ -341,17 +400,18 @@ template <int T>
 cudaError_t launch_bfs1(const Params1& p, int blocks, cudaStream_t st) {
     void* args[] = {(void*)&p};
     const void* k = p.frontier_sort != BFS_SORT_NONE ? (const void*)bfs1_kernel<T, true> : (const void*)bfs1_kernel<T, false>;
-    return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(T), args, BFS1_DYN_SMEM, st);
+    return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(T), args, bfs1_dyn_smem<T>(), st);
 }
 
 template <int T>
 int max_coop_blocks(int blocks_per_sm) {
     int per_sm = 0;
     int per_sm_sorted = 0;
-    cudaFuncSetAttribute(bfs1_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
-    cudaFuncSetAttribute(bfs1_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BFS1_DYN_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T, false>, T, BFS1_DYN_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sorted, bfs1_kernel<T, true>, T, BFS1_DYN_SMEM);
+    const size_t dyn = bfs1_dyn_smem<T>();
+    cudaFuncSetAttribute(bfs1_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaFuncSetAttribute(bfs1_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs1_kernel<T, false>, T, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sorted, bfs1_kernel<T, true>, T, dyn);
     per_sm = std::min(per_sm, per_sm_sorted);  // one grid size whichever instantiation runs
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);

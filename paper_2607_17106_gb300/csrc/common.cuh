@@ -136,12 +136,15 @@ struct GridBarrier {
 // leaves its loop.  Returns false when the barrier was aborted.
 // `before_arrival` runs on thread 0 after the CTA's __syncthreads and before
 // the arrival, so its writes are published by the same release.
+// `after_open` runs on thread 0 once the barrier is open (after the acquire,
+// beside the read of the abort flag, so that their loads overlap); what it
+// stores in shared memory is visible to the CTA when grid_sync returns.
 struct NoArrivalWork {
     __device__ void operator()() const {}
 };
-template <typename F = NoArrivalWork>
+template <typename F = NoArrivalWork, typename A = NoArrivalWork>
 __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsigned& target, int64_t timeout_ns,
-                                          F before_arrival = F()) {
+                                          F before_arrival = F(), A after_open = A()) {
     __shared__ int s_ok;
     __syncthreads();
     target += nblocks;
@@ -167,7 +170,13 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsi
                 }
             }
         }
+#ifndef BFS_BAR_POSTCHECK
+#define BFS_BAR_POSTCHECK 1
+#endif
+        if (ok) after_open();
+#if BFS_BAR_POSTCHECK
         if (ld_volatile_i32(&b->abort)) ok = 0;
+#endif
         s_ok = ok;
     }
     __syncthreads();

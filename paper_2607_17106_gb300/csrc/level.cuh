@@ -373,20 +373,20 @@ struct PullWarpSmem {
     int nl;
 };
 
-// The open words of a round's dense pull blocks, shared by the CTA's warps.
+// A round of the list-driven pull (pull_level_list): the new bits found for
+// the P words the CTA's warps own in the round (slot = warp * 32 + lane); the
+// round's unvisited vertices are listed in dynamic shared memory as 16-bit
+// (slot, bit) entries.
 template <int T>
-struct PullCtaSmem {
-    int n;         // words in the list
-    int next;      // cursor of the warps draining it
-    int word[T];   // word index of P
-    unsigned pw[T];  // its P word
-    int ns, snext;   // sparse blocks of the round and their cursor
-    long long sblk[T / 32];
+struct PullListSmem {
+    int n;           // unvisited vertices listed in the round
+    int next;        // cursor of the warps draining the list
+    unsigned nb[T];  // bits of F_{i+1} found in each slot's word
 };
 
 // Shared memory of a CTA running level kernels.  Push levels use the tile
-// scratch and the warps' next-queue staging; pull levels use the per-warp
-// pull scratch; no level uses both, so they share storage.
+// scratch and the warps' next-queue staging; pull levels use the round's
+// new-bit words; no level uses both, so they share storage.
 template <int T>
 struct TileSmem {
     union {
@@ -399,10 +399,7 @@ struct TileSmem {
             int32_t qb[(T / 32) * QBUF];
             int32_t qe[(T / 32) * QBUF];
         } t;
-        struct {
-            PullWarpSmem w[T / 32];
-            PullCtaSmem<T> c;
-        } pull;
+        PullListSmem<T> list;
     };
     int scan_tmp[33];
     unsigned long long red[T / 32];
@@ -801,9 +798,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 }
 
 // Record a vertex found by a pull scan (parent u).  Any lane, any time.
-__device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWarpSmem& ws, int slot, int v, int u,
+__device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, unsigned* nb, int slot, int v, int u,
                                            int b0, int e) {
-    atomicOr(&ws.nb[slot], 1u << (v & 31));
+    atomicOr(nb + slot, 1u << (v & 31));
     L.depth[v] = L.level + 1;
     if (L.parent) L.parent[v] = u;
     L.ef += (unsigned long long)(p.symmetric ? (e - b0) : (__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v)));
@@ -812,7 +809,7 @@ __device__ __forceinline__ void pull_found(const Params1& p, LevelCtx& L, PullWa
 
 // The deferred rows of the block, each scanned by the whole warp.  Warp-uniform.
 template <bool NC>
-__device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, PullWarpSmem& ws,
+__device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, PullWarpSmem& ws, unsigned* nb,
                                                const uint32_t* f_cur) {
     __syncwarp();
     const int nl = min(ws.nl, 32);
@@ -838,7 +835,7 @@ __device__ __forceinline__ void pull_long_rows(const Params1& p, LevelCtx& L, Pu
                 if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[q], __ffs(hb) - 1);
             }
         }
-        if (hit >= 0 && lane == 0) pull_found(p, L, ws, ws.ls[r], v, hit, bl, el);
+        if (hit >= 0 && lane == 0) pull_found(p, L, nb, ws.ls[r], v, hit, bl, el);
     }
     __syncwarp();
     if (lane == 0) ws.nl = 0;
@@ -963,7 +960,7 @@ __device__ __forceinline__ void pull_block_sparse(const Params1& p, LevelCtx& L,
                     st[q] = TEST;
                 } else if (st[q] == TEST) {
                     if ((x1[q] >> (u[q] & 31)) & 1u) {
-                        pull_found(p, L, ws, sl[q], v[q], u[q], b0[q], e[q]);
+                        pull_found(p, L, ws.nb, sl[q], v[q], u[q], b0[q], e[q]);
                         st[q] = IDLE;
                     } else if (++j[q] >= e[q]) {
                         st[q] = IDLE;
@@ -978,7 +975,7 @@ __device__ __forceinline__ void pull_block_sparse(const Params1& p, LevelCtx& L,
             for (int q = 0; q < PULL_SLOTS; ++q) {
                 const unsigned dm = __ballot_sync(FULL, defer[q]);
                 if (dm) {
-                    if (ws.nl + __popc(dm) > 32) pull_long_rows<NC>(p, L, ws, f_cur);
+                    if (ws.nl + __popc(dm) > 32) pull_long_rows<NC>(p, L, ws, ws.nb, f_cur);
                     if (defer[q]) {
                         const int slot = ws.nl + __popc(dm & lanemask_lt());
                         ws.lv[slot] = v[q];
@@ -994,7 +991,7 @@ __device__ __forceinline__ void pull_block_sparse(const Params1& p, LevelCtx& L,
                 }
             }
         }
-        pull_long_rows<NC>(p, L, ws, f_cur);
+        pull_long_rows<NC>(p, L, ws, ws.nb, f_cur);
         if (wl < p.W) {
             const unsigned nb = ws.nb[lane];
             f_next[wl] = nb;
@@ -1027,113 +1024,187 @@ __device__ __forceinline__ void pull_level(const Params1& p, LevelCtx& L, const 
     }
 }
 
-// Pull level with the dense words of a CTA shared by all its warps.  CTA c
-// takes the blocks c, c + G, c + 2G, ... (G CTAs), one per warp per round.  A
-// warp finishes a sparse block itself (pull_block_sparse); a dense block's
-// open words go to a CTA list, which all warps then drain PULL_WPI words at a
-// time through a shared-memory cursor.  The cost of a dense block (the
-// longest scan among the lanes of each group of words) is thereby spread over
-// the CTA's warps instead of being carried by one.  Block-uniform.
+// Listed vertices a lane scans at once in the list-driven pull (1 and 4
+// measured slower on RMAT, ER and BA).
+constexpr int PULL_LPI = 2;
+
+// Scans of up to PULL_LPI listed vertices per lane (v < 0: none), as in
+// pull_words_scan: ascending in-neighbours, the first one in F_i is the
+// parent; rows still open after `serial` entries are finished by the whole
+// warp, 4 x 32 entries a step.  Found vertices set their bit in the slot's
+// shared-memory word nb[sl].  Warp-uniform.
+template <bool NC>
+__device__ __forceinline__ void pull_list_scan(const Params1& p, LevelCtx& L, unsigned* nb, const uint32_t* f_cur,
+                                               const int (&v)[PULL_LPI], const int (&sl)[PULL_LPI], int serial) {
+    const unsigned lane = lane_id();
+    int beg[PULL_LPI], end[PULL_LPI], j[PULL_LPI], par[PULL_LPI];
+    bool found[PULL_LPI];
+#pragma unroll
+    for (int q = 0; q < PULL_LPI; ++q) {
+        beg[q] = v[q] >= 0 ? __ldg(p.csc_ptr + v[q]) : 0;
+        end[q] = v[q] >= 0 ? __ldg(p.csc_ptr + v[q] + 1) : 0;
+        j[q] = beg[q];
+        par[q] = -1;
+        found[q] = false;
+    }
+    // software-pipelined scan: each step tests the current entry's F_i word
+    // and loads the next entry, so a step costs one memory round trip (two
+    // or four entries a step measured no faster)
+    int u[PULL_LPI];
+#pragma unroll
+    for (int q = 0; q < PULL_LPI; ++q) u[q] = j[q] < end[q] ? __ldg(p.csc_col + j[q]) : -1;
+    for (int step = 0; step < serial; ++step) {
+        unsigned fw[PULL_LPI];
+        int un[PULL_LPI];
+        bool live = false;
+#pragma unroll
+        for (int q = 0; q < PULL_LPI; ++q) {
+            live |= u[q] >= 0;
+            fw[q] = u[q] >= 0 ? ld_word<NC>(f_cur, u[q] >> 5) : 0u;
+            un[q] = (u[q] >= 0 && j[q] + 1 < end[q] && step + 1 < serial) ? __ldg(p.csc_col + j[q] + 1) : -1;
+        }
+        if (!live) break;
+#pragma unroll
+        for (int q = 0; q < PULL_LPI; ++q) {
+            if (u[q] < 0) continue;
+            if ((fw[q] >> (u[q] & 31)) & 1u) {
+                found[q] = true;
+                par[q] = u[q];
+                u[q] = -1;
+            } else {
+                ++j[q];
+                u[q] = un[q];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PULL_LPI; ++q) {
+        unsigned rm = __ballot_sync(0xffffffffu, v[q] >= 0 && !found[q] && j[q] < end[q]);
+        while (rm) {
+            const int l = __ffs(rm) - 1;
+            const int bl = __shfl_sync(0xffffffffu, j[q], l);
+            const int el = __shfl_sync(0xffffffffu, end[q], l);
+            int hit = -1;
+            for (int base = bl; base < el && hit < 0; base += 128) {
+                int uu[4];
+                unsigned fw[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int idx = base + t * 32 + (int)lane;
+                    uu[t] = idx < el ? __ldg(p.csc_col + idx) : -1;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) fw[t] = uu[t] >= 0 ? ld_word<NC>(f_cur, uu[t] >> 5) : 0u;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const unsigned hb = __ballot_sync(0xffffffffu, uu[t] >= 0 && ((fw[t] >> (uu[t] & 31)) & 1u));
+                    if (hb && hit < 0) hit = __shfl_sync(0xffffffffu, uu[t], __ffs(hb) - 1);
+                }
+            }
+            if ((int)lane == l && hit >= 0) {
+                found[q] = true;
+                par[q] = hit;
+            }
+            rm &= rm - 1;
+        }
+        if (found[q]) {
+            atomicOr(nb + sl[q], 1u << (v[q] & 31));
+            L.depth[v[q]] = L.level + 1;
+            if (L.parent) L.parent[v[q]] = par[q];
+            L.ef += (unsigned long long)(p.symmetric ? (end[q] - beg[q])
+                                                     : (__ldg(p.row_ptr + v[q] + 1) - __ldg(p.row_ptr + v[q])));
+            L.cnt += 1;
+        }
+    }
+}
+
+// Vertex of round-list entry e (slot = warp * 32 + lane of the word's owner,
+// bit) in round r.
+__device__ __forceinline__ int pull_list_vertex(int e, long long r, long long G, long long S) {
+    const int s2 = e >> 5;
+    const long long w = r + (long long)(s2 >> 5) * G + (long long)(s2 & 31) * S;
+    return (int)(w * 32 + (e & 31));
+}
+
+// Pull level of the persistent kernel, driven by a list of the unvisited
+// vertices (Section 5, loop order d -> s).  Blocks of 32 words of P are
+// strided over the vertex range as in pull_level (block b = words b + l * S,
+// so a cluster of costly vertices is spread over many CTAs); CTA c owns the
+// blocks c, c + G, c + 2G, ... (G CTAs), one per warp per round.  In each
+// round every warp reads its block's 32 words and appends their unvisited
+// vertices to the CTA's list in shared memory; the warps then drain the list
+// 32 * PULL_LPI entries at a time, so every lane scans a vertex that is
+// still open, however sparse the words are, and the cost of a dense block is
+// spread over all the CTA's warps.  New bits collect in shared memory per
+// word and are stored with plain stores by the word's owner after the round.
+// `lst` holds T * 32 entries.  Block-uniform.
 template <bool NC, int T>
-__device__ void pull_level_cta(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
-                               PullWarpSmem& ws, PullCtaSmem<T>& cs) {
+__device__ void pull_level_list(const Params1& p, LevelCtx& L, const uint32_t* f_cur, uint32_t* f_next,
+                                PullListSmem<T>& ls, uint16_t* lst) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int NW = T / 32;
+    static_assert(T * 32 <= 65536, "16-bit list entries");
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const long long S = (p.W + 31) >> 5;
     const long long G = gridDim.x;
-#if BFS_LEVEL_PHASES
-    const uint64_t t_start = globaltimer_ns();
-    uint64_t t_a = 0, t_b = 0;
-#endif
+    const int serial = max(1, min(p.pull_serial, PULL_SERIAL_MAX));
     for (long long r = blockIdx.x; r < S; r += G * NW) {  // CTA-uniform
         if (threadIdx.x == 0) {
-            cs.n = 0;
-            cs.next = 0;
-            cs.ns = 0;
-            cs.snext = 0;
+            ls.n = 0;
+            ls.next = 0;
         }
         __syncthreads();
         const long long bi = r + (long long)warp * G;
-        if (bi < S) {  // warp-uniform
-            const long long wl = bi + lane * S;
-            const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : FULL;
-            unsigned um;
-            int excl;
-            const int U = pull_block_census(pwl, um, excl);
-            if (U == 0) {
-                if (wl < p.W) f_next[wl] = 0;
-            } else if (U <= PULL_SPARSE_MAX) {
-                // finished after the dense words, by whichever warp is free
-                if (lane == 0) cs.sblk[atomicAdd(&cs.ns, 1)] = bi;
-            } else {
-                if (wl < p.W && pwl == FULL) f_next[wl] = 0;
-                const bool add = wl < p.W && pwl != FULL;
-                const unsigned am = __ballot_sync(FULL, add);
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&cs.n, __popc(am));
-                base = __shfl_sync(FULL, base, 0);
-                if (add) {
-                    const int k = base + __popc(am & lanemask_lt());  // < NW * 32 = T
-                    cs.word[k] = (int)wl;
-                    cs.pw[k] = pwl;
-                }
-            }
+        const long long wl = bi + (long long)lane * S;
+        const bool own = bi < S && wl < p.W;
+        const unsigned pwl = own ? ld_word<NC>(p.P, wl) : FULL;
+        const int slot = (int)(warp * 32 + lane);
+        ls.nb[slot] = 0;
+        unsigned um = ~pwl;
+        const int c = __popc(um);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if ((int)lane >= o) incl += y;
         }
-#if BFS_LEVEL_PHASES
-        const uint64_t t_a_end = globaltimer_ns();  // this warp's phase A done
-        t_a += t_a_end - t_start;
-#endif
+        const int tot = __shfl_sync(FULL, incl, 31);
+        int base = 0;
+        if (lane == 0 && tot) base = atomicAdd(&ls.n, tot);
+        int k = __shfl_sync(FULL, base, 0) + incl - c;
+        while (um) {
+            const int b = __ffs(um) - 1;
+            um &= um - 1;
+            lst[k++] = (uint16_t)(slot * 32 + b);
+        }
         __syncthreads();
-#if BFS_LEVEL_PHASES
-        const uint64_t t_b0 = globaltimer_ns();
-#endif
-        const int nlist = cs.n;
+        const int n = ls.n;
         for (;;) {  // warp-uniform
             int k0 = 0;
-            if (lane == 0) k0 = atomicAdd(&cs.next, PULL_WPI);
+            if (lane == 0) k0 = atomicAdd(&ls.next, 32 * PULL_LPI);
             k0 = __shfl_sync(FULL, k0, 0);
-            if (k0 >= nlist) break;
-            long long wv[PULL_WPI];
-            unsigned pw[PULL_WPI];
+            if (k0 >= n) break;
+            int v[PULL_LPI], sl[PULL_LPI];
 #pragma unroll
-            for (int k = 0; k < PULL_WPI; ++k) {
-                const bool has = k0 + k < nlist;
-                wv[k] = has ? cs.word[k0 + k] : -1;
-                pw[k] = has ? cs.pw[k0 + k] : FULL;
+            for (int q = 0; q < PULL_LPI; ++q) {
+                const int idx = k0 + q * 32 + (int)lane;
+                v[q] = -1;
+                sl[q] = 0;
+                if (idx < n) {
+                    const int e = lst[idx];
+                    v[q] = pull_list_vertex(e, r, G, S);
+                    sl[q] = e >> 5;
+                }
             }
-            pull_words<NC>(p, L, f_cur, f_next, wv, pw);
+            pull_list_scan<NC>(p, L, ls.nb, f_cur, v, sl, serial);
         }
-        const int nsparse = cs.ns;
-        for (;;) {  // warp-uniform: the round's sparse blocks
-            int k = 0;
-            if (lane == 0) k = atomicAdd(&cs.snext, 1);
-            k = __shfl_sync(FULL, k, 0);
-            if (k >= nsparse) break;
-            const long long bi = cs.sblk[k];
-            const long long wl = bi + lane * S;
-            const unsigned pwl = wl < p.W ? ld_word<NC>(p.P, wl) : FULL;
-            unsigned um;
-            int excl;
-            const int U = pull_block_census(pwl, um, excl);
-            pull_block_sparse<NC>(p, L, f_cur, f_next, ws, bi, S, wl, pwl, um, excl, U);
+        __syncthreads();
+        if (own) {
+            const unsigned nb = ls.nb[slot];
+            f_next[wl] = nb;
+            if (nb) p.P[wl] = pwl | nb;
         }
-#if BFS_LEVEL_PHASES
-        t_b += globaltimer_ns() - t_b0;  // this warp's phase B (its share of the list)
-#endif
-        __syncthreads();  // the list is drained before the next round resets it
     }
-#if BFS_LEVEL_PHASES
-    // per level: sum and max over warps of phase A (own block) and phase B
-    // (draining the CTA list) times, in the second half of the level log
-    if (lane == 0 && p.log && L.level < p.log_cap / 2) {
-        bfs_level_record* r = &p.log[p.log_cap / 2 + L.level];
-        atomicAdd((unsigned long long*)&r->f, (unsigned long long)t_a);
-        atomicMax((unsigned long long*)&r->e_f, (unsigned long long)t_a);
-        atomicAdd((int*)&r->dir, (int)(t_b / 1000));
-        atomicMax((int*)&r->level, (int)(t_b / 10));
-    }
-#endif
 }
 
 // ------------------------------------------------------------ conversions

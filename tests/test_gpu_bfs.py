@@ -33,8 +33,10 @@ def _graph_pair(n, src, dst):
 
 def _run(g, n, sources, opt=None, with_parent=True):
     k = len(sources)
-    depth = torch.empty(k * n, dtype=torch.int32, device="cuda")
-    parent = torch.empty(k * n, dtype=torch.int32, device="cuda") if with_parent else None
+    # a sentinel, so that an entry the run leaves unwritten cannot pass for an
+    # earlier run's result left in reused memory
+    depth = torch.full((k * n,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    parent = torch.full((k * n,), 0x5A5A5A5A, dtype=torch.int32, device="cuda") if with_parent else None
     src = np.asarray(sources, np.int32)
     g.run(src, depth, parent, opt)
     g.sync()
@@ -369,20 +371,27 @@ def test_many_searches_in_one_launch_match_the_oracle():
     # persistent launch: an isolated source, a two-vertex component, the same
     # hub twice, a path end, mixed with ordinary sources; and the same sources
     # one call each
+    # (the -1 rows of a search are stored during the previous search's first
+    # pull level; with n % 4 != 0 most rows start off a 16-byte boundary)
     nr, rs, rd = graphgen.rmat(13, 16, seed=31)
     a = 2500
     src = np.concatenate([rs, np.arange(nr, nr + a - 1), [nr + a + 1]]).astype(np.int32)
     dst = np.concatenate([rd, np.arange(nr + 1, nr + a), [nr + a + 2]]).astype(np.int32)
-    n = nr + a + 4  # nr + a + 3 stays isolated
-    adj, g = _graph_pair(n, src, dst)
-    deg = np.diff(adj.row_ptr)
-    hub = int(np.argmax(deg))
-    srcs = [nr + a + 3, nr + a + 1, hub, hub, nr, 7] + graphgen.sample_sources(n, src, dst, 6, seed=5).tolist()
-    for o in (bg.options(batch=0), bg.options(batch=0, block_threads=512), bg.options(batch=0, policy=bg.BFS_POLICY_PULL)):
-        dd, pp = _run(g, n, srcs, o)
-        _check(adj, srcs, dd, pp)
-    d1 = np.stack([_run(g, n, [s], bg.options(batch=0))[0][0] for s in srcs])
-    assert np.array_equal(d1, dd)
+    for pad in (0, 1, 3):
+        n = nr + a + 4 + pad  # nr + a + 3 and the padding stay isolated
+        adj, g = _graph_pair(n, src, dst)
+        deg = np.diff(adj.row_ptr)
+        hub = int(np.argmax(deg))
+        srcs = [nr + a + 3, nr + a + 1, hub, hub, nr, 7] + graphgen.sample_sources(n, src, dst, 6, seed=5).tolist()
+        opts = [bg.options(batch=0)]
+        if pad == 0:
+            opts += [bg.options(batch=0, block_threads=512), bg.options(batch=0, policy=bg.BFS_POLICY_PULL)]
+        for o in opts:
+            dd, pp = _run(g, n, srcs, o)
+            _check(adj, srcs, dd, pp)
+        d1 = np.stack([_run(g, n, [s], bg.options(batch=0))[0][0] for s in srcs])
+        assert np.array_equal(d1, dd)
+        g.free()
 
 
 def test_edge_cases_tiny_and_isolated():

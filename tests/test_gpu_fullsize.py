@@ -56,23 +56,39 @@ def full(request):
 
 
 def test_single_source_full_size_sampled(full):
+    # the bench's step: the 64 sources one after another in one persistent
+    # launch (each search's -1 rows stored during the previous search)
     name, n, s, d, srcs, g, adj = full
-    depth = torch.empty(n, dtype=torch.int32, device="cuda")
-    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    k = len(srcs)
+    depth = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    parent = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    g.run(srcs, depth, parent, bg.options(batch=0))
+    g.sync()
     for j in (0, 17, 63):
-        g.run(srcs[j:j + 1], depth, parent, bg.options(batch=0))
-        g.sync()
-        dd, pp = depth.cpu().numpy(), parent.cpu().numpy()
+        dd, pp = depth[j].cpu().numpy(), parent[j].cpu().numpy()
         ref, _ = oracle.bfs(adj, int(srcs[j]), with_parent=False)
         assert np.array_equal(dd, ref), (name, j)
         assert oracle.validate(adj, int(srcs[j]), dd, pp) == 0, (name, j)
+    rp, col = g.csr()
+    row_ptr = torch.from_numpy(rp.astype(np.int64)).cuda()
+    colt = torch.from_numpy(col.astype(np.int64)).cuda()
+    for j in range(1, k, 5):
+        assert _edge_properties_hold(row_ptr, colt, depth[j].long(), int(srcs[j])), (name, j)
+        assert int(parent[j][int(srcs[j])]) == int(srcs[j])
+        assert int((depth[j] == 0x5A5A5A5A).sum()) == 0 and int((parent[j] == 0x5A5A5A5A).sum()) == 0
+    # one search per call gives the same depths
+    one = torch.empty(n, dtype=torch.int32, device="cuda")
+    for j in (5, 40):
+        g.run(srcs[j:j + 1], one, None, bg.options(batch=0))
+        g.sync()
+        assert torch.equal(one, depth[j]), (name, j)
 
 
 def test_batched_full_size_sampled_and_properties(full):
     name, n, s, d, srcs, g, adj = full
     k = len(srcs)
-    depth = torch.empty((k, n), dtype=torch.int32, device="cuda")
-    parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
+    depth = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    parent = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
     g.run(srcs, depth, parent, bg.options(batch=1))
     g.sync()
     for j in (0, 31, 63):  # whole lanes against the oracle

@@ -95,8 +95,8 @@ def _single(g, n, srcs, js, opt, adj, what):
 
 def _batched(g, n, srcs, lanes, opt, adj, what, props_every=0):
     k = len(srcs)
-    depth = torch.empty((k, n), dtype=torch.int32, device="cuda")
-    parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
+    depth = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+    parent = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
     g.run(srcs, depth, parent, opt)
     g.sync()
     for j in lanes:
