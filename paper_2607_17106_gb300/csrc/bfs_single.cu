@@ -123,9 +123,16 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     // the -1 rows of the next search of this launch were stored during the
     // current one (grid-uniform: every CTA takes the same directions)
     bool prefilled = false, prefill_next = false;
+    // counters of the level about to start (|F_i|, chunk units, e_f): set by
+    // the init, or read by thread 0 right after the level barrier opens
+    // (s_cnt_ok), else read at the top of the level
+    __shared__ unsigned long long s_cnt[3];
+    const unsigned warp = threadIdx.x >> 5;
     for (int si = 0; si < nsearch; ++si) {
     int32_t* const depth = p.depth + (int64_t)si * p.n;
     int32_t* const parent = p.parent ? p.parent + (int64_t)si * p.n : nullptr;
+    Counters* const cs = ctl->slot + 3 * (si & 1);
+    bool s_cnt_ok = false;
     if (p.do_init) {
         const int s = p.srcs ? __ldg(p.srcs + si) : p.src_value;
         for (long long w = gtid; w < p.W; w += gthreads) {
@@ -139,31 +146,38 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (parent) fill_minus1(parent, p.n, gtid, gthreads);
         }
         prefilled = false;
-        if (gtid == 0) {
+        __syncthreads();  // the CTA's warps have read s_cnt of the previous search's last level
+        if (threadIdx.x == 0) {
+            // every CTA knows level 0's counters without reading them back
             const int rb = __ldg(p.row_ptr + s), re = __ldg(p.row_ptr + s + 1);
             const int deg = re - rb;
-            p.Q0[0] = make_int4(s, rb, re, 0);
-            int nch = deg >= p.chunk ? (deg + p.chunk - 1) / p.chunk : 0;
-            for (int c = 0; c < nch; ++c) p.U0[c] = make_int2(s, c);
-            for (int k = 1; k < 3; ++k) {  // a previous search of this launch used them
-                ctl->slot[k].q_len = 0;
-                ctl->slot[k].u_len = 0;
-                ctl->slot[k].e_f = 0;
-                ctl->slot[k].conv = 0;
-                ctl->slot[k].e_len = 0;
+            const int nch = deg >= p.chunk ? (deg + p.chunk - 1) / p.chunk : 0;
+            s_cnt[0] = 1;
+            s_cnt[1] = (unsigned long long)nch;
+            s_cnt[2] = (unsigned long long)deg;
+            if (blockIdx.x == 0) {
+                p.Q0[0] = make_int4(s, rb, re, 0);
+                for (int c = 0; c < nch; ++c) p.U0[c] = make_int2(s, c);
+                for (int k = 1; k < 3; ++k) {  // the search before the previous one used them
+                    cs[k].q_len = 0;
+                    cs[k].u_len = 0;
+                    cs[k].e_f = 0;
+                    cs[k].conv = 0;
+                    cs[k].e_len = 0;
+                }
+                cs[0].q_len = 1;
+                cs[0].u_len = nch;
+                cs[0].e_f = deg;
+                cs[0].conv = 0;
+                cs[0].e_len = 0;
+                ctl->next_level = 0;
+                ctl->prev_dir = BFS_DIR_PUSH_QUEUE;
+                ctl->bm_valid = -1;
+                ctl->q_valid = 0;
+                ctl->done = 0;
+                ctl->m_u = p.m - deg;
+                ctl->f_prev = 0;
             }
-            ctl->slot[0].q_len = 1;
-            ctl->slot[0].u_len = nch;
-            ctl->slot[0].e_f = deg;
-            ctl->slot[0].conv = 0;
-            ctl->slot[0].e_len = 0;
-            ctl->next_level = 0;
-            ctl->prev_dir = BFS_DIR_PUSH_QUEUE;
-            ctl->bm_valid = -1;
-            ctl->q_valid = 0;
-            ctl->done = 0;
-            ctl->m_u = p.m - deg;
-            ctl->f_prev = 0;
         }
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         // after the barrier: ordered after every -1 store of the rows
@@ -171,25 +185,28 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             depth[s] = 0;
             if (parent) parent[s] = s;
         }
+        level = 0;
+        prev_dir = BFS_DIR_PUSH_QUEUE;
+        bm_valid = -1;
+        q_valid = 0;
+        m_u = p.m - (long long)s_cnt[2];
+        f_prev = 0;
+        done = false;
+        s_cnt_ok = true;
+    } else {
+        level = __ldcg(&ctl->next_level);
+        prev_dir = __ldcg(&ctl->prev_dir);
+        bm_valid = __ldcg(&ctl->bm_valid);
+        q_valid = __ldcg(&ctl->q_valid);
+        m_u = __ldcg(&ctl->m_u);
+        f_prev = __ldcg(&ctl->f_prev);
+        done = __ldcg(&ctl->done) != 0;
     }
-
-    level = __ldcg(&ctl->next_level);
-    prev_dir = __ldcg(&ctl->prev_dir);
-    bm_valid = __ldcg(&ctl->bm_valid);
-    q_valid = __ldcg(&ctl->q_valid);
-    m_u = __ldcg(&ctl->m_u);
-    f_prev = __ldcg(&ctl->f_prev);
-    done = __ldcg(&ctl->done) != 0;
     const int level_end = level + p.level_count;
-    const unsigned warp = threadIdx.x >> 5;
 
-    // counters of the level about to start (|F_i|, chunk units, e_f), read
-    // by thread 0 right after the level barrier opens (s_cnt_ok), else here
-    __shared__ unsigned long long s_cnt[3];
-    bool s_cnt_ok = false;
     while (!done && level < level_end) {
-        Counters* cur = &ctl->slot[level % 3];
-        Counters* nxt = &ctl->slot[(level + 1) % 3];
+        Counters* cur = &cs[level % 3];
+        Counters* nxt = &cs[(level + 1) % 3];
         int4* q_cur = (level & 1) ? p.Q1 : p.Q0;
         unsigned long long cv[3];
         if (s_cnt_ok) {
@@ -273,7 +290,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             q_valid = level;
         }
         if (gtid == 0) {
-            Counters* z = &ctl->slot[(level + 2) % 3];
+            Counters* z = &cs[(level + 2) % 3];
             z->q_len = 0;
             z->u_len = 0;
             z->e_f = 0;
@@ -298,7 +315,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.precheck = push_precheck(m_u, p.m, e_f);
         if (dir == BFS_DIR_PULL) {
 #ifndef BFS_PREFILL
-#define BFS_PREFILL 1
+#define BFS_PREFILL 0
 #endif
             if (BFS_PREFILL && !prefill_next && p.do_init && si + 1 < nsearch) {
                 // the first pull level of a search is long and latency-bound:
@@ -364,8 +381,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     }
     prefilled = prefill_next;
     prefill_next = false;
-    // every CTA is past this search's last level before the next one starts
-    if (si + 1 < nsearch && !grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+    // No barrier before the next search: after the last level's barrier a CTA
+    // reads only its own shared memory (s_cnt) before it leaves the loop, so
+    // the next search's init may overwrite P, the queues and the other
+    // counter set while slower CTAs are still leaving.
     }  // searches
     if (gtid == 0) {
         ctl->next_level = level;

@@ -18,7 +18,11 @@ struct Counters {
 
 struct Ctl1 {
     GridBarrier bar;
-    Counters slot[3];
+    // level i of search si of a launch counts in slot[3 * (si & 1) + i % 3]:
+    // consecutive searches use different sets, so one search's first CTA
+    // can reset its set while another CTA still reads the previous search's
+    // last counters
+    Counters slot[6];
     // loop state carried between launches
     int32_t next_level;
     int32_t prev_dir;
