@@ -120,9 +120,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     int level = 0, prev_dir = BFS_DIR_PUSH_QUEUE, bm_valid = -1, q_valid = 0;
     long long m_u = 0, f_prev = 0;
     bool done = false;
-    // the -1 rows of the next search of this launch were stored during the
-    // current one (grid-uniform: every CTA takes the same directions)
-    bool prefilled = false, prefill_next = false;
     // counters of the level about to start (|F_i|, chunk units, e_f): set by
     // the init, or read by thread 0 right after the level barrier opens
     // (s_cnt_ok), else read at the top of the level
@@ -141,11 +138,8 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (w == p.W - 1 && (p.n & 31)) bits |= ~((1u << (p.n & 31)) - 1u);  // phantom vertices
             p.P[w] = bits;
         }
-        if (!prefilled) {
-            fill_minus1(depth, p.n, gtid, gthreads);
-            if (parent) fill_minus1(parent, p.n, gtid, gthreads);
-        }
-        prefilled = false;
+        fill_minus1(depth, p.n, gtid, gthreads);
+        if (parent) fill_minus1(parent, p.n, gtid, gthreads);
         __syncthreads();  // the CTA's warps have read s_cnt of the previous search's last level
         if (threadIdx.x == 0) {
             // every CTA knows level 0's counters without reading them back
@@ -314,16 +308,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.err = &p.ctl->bar.err;
         L.precheck = push_precheck(m_u, p.m, e_f);
         if (dir == BFS_DIR_PULL) {
-#ifndef BFS_PREFILL
-#define BFS_PREFILL 0
-#endif
-            if (BFS_PREFILL && !prefill_next && p.do_init && si + 1 < nsearch) {
-                // the first pull level of a search is long and latency-bound:
-                // the next search's -1 rows are stored beside its scans
-                fill_minus1(p.depth + (int64_t)(si + 1) * p.n, p.n, gtid, gthreads);
-                if (p.parent) fill_minus1(p.parent + (int64_t)(si + 1) * p.n, p.n, gtid, gthreads);
-                prefill_next = true;
-            }
             pull_level_list<false, T>(p, L, f_cur, f_nxt, sm.list, reinterpret_cast<uint16_t*>(bfs1_dyn));
         } else {
             push_level<T, SORT>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
@@ -379,8 +363,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         (void)done_level;
 #endif
     }
-    prefilled = prefill_next;
-    prefill_next = false;
     // No barrier before the next search: after the last level's barrier a CTA
     // reads only its own shared memory (s_cnt) before it leaves the loop, so
     // the next search's init may overwrite P, the queues and the other

@@ -371,8 +371,8 @@ def test_many_searches_in_one_launch_match_the_oracle():
     # persistent launch: an isolated source, a two-vertex component, the same
     # hub twice, a path end, mixed with ordinary sources; and the same sources
     # one call each
-    # (the -1 rows of a search are stored during the previous search's first
-    # pull level; with n % 4 != 0 most rows start off a 16-byte boundary)
+    # (with n % 4 != 0 most output rows start off a 16-byte boundary, where
+    # the -1 stores of a row switch from 4-byte to 16-byte stores)
     nr, rs, rd = graphgen.rmat(13, 16, seed=31)
     a = 2500
     src = np.concatenate([rs, np.arange(nr, nr + a - 1), [nr + a + 1]]).astype(np.int32)

@@ -57,7 +57,7 @@ def full(request):
 
 def test_single_source_full_size_sampled(full):
     # the bench's step: the 64 sources one after another in one persistent
-    # launch (each search's -1 rows stored during the previous search)
+    # launch, with no grid barrier between consecutive searches
     name, n, s, d, srcs, g, adj = full
     k = len(srcs)
     depth = torch.full((k, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
