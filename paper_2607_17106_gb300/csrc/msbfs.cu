@@ -50,6 +50,7 @@ struct CountersMS {
     unsigned long long conv;   // cursor of a masks -> active-list conversion
     unsigned long long lanes;  // OR of the frontier masks: lanes that can still find vertices
     unsigned long long done_e; // degree sum of the vertices that the level left seen by every live lane
+    unsigned long long pull_next;  // pull level: cursor of the warps over the words of the vertex range
 };
 
 struct CtlMS {
@@ -170,6 +171,10 @@ constexpr int MS_LONG_ITEMS = 4;  // entries a thread tests per long-row chunk
 #endif
 constexpr int MS_PULL_R = BFS_MS_PULL_R;  // in-neighbours loaded per serial pull step
 constexpr int MS_COOP_U = 4;  // 32-entry groups a warp loads per step when it finishes a long row
+// Words a warp takes at a time in a pull level: one while many vertices
+// still miss live lanes (costly words: finest balance), eight once few do
+// (the takes of one word each then queue on the cursor's atomics).
+constexpr int MS_PULL_CHUNK_DENSE = 1, MS_PULL_CHUNK_SPARSE = 8;
 
 struct MsSmem {
     int32_t* depth[64];
@@ -200,6 +205,8 @@ struct MsLevel {
     unsigned long long done_e;  // degree sum of vertices now seen by every live lane (this thread's share)
     int32_t* qbuf;
     int qn;                  // staged appends (warp-uniform)
+    unsigned long long* cursor;  // pull: next word to take (zero when the level starts)
+    int pull_chunk;              // pull: words a warp takes at a time
     bool write_depth;        // depths of F_{i+1} are written now (levels past the history)
 };
 
@@ -381,11 +388,22 @@ extern __shared__ __align__(16) unsigned short ms_pidx_smem[];
 __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, MsSmem& sm, const uint64_t* f_cur) {
     const unsigned lane = lane_id();
     unsigned short* pidx = ms_pidx_smem + (threadIdx.x >> 5) * (64 * 32);
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int dnext = L.level + 1;
     const long long W = (g.n + 31) >> 5;
     const unsigned long long* F = (const unsigned long long*)f_cur;
-    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < W; w += nwarps) {
+    // warps take L.pull_chunk words at a time from a level-wide cursor: the
+    // cost of a word varies by orders of magnitude (hubs, early exits), and a
+    // fixed deal left most warps waiting at the level barrier.  The next take
+    // is requested when a chunk starts, so its round trip overlaps the work.
+    const unsigned long long chunk = (unsigned long long)L.pull_chunk;
+    unsigned long long take = 0;
+    if (lane == 0) take = atomicAdd(L.cursor, chunk);
+    for (;;) {  // warp-uniform
+        const long long w0 = (long long)__shfl_sync(0xffffffffu, take, 0);
+        if (w0 >= W) break;
+        if (lane == 0) take = atomicAdd(L.cursor, chunk);
+        const long long w1 = min(w0 + (long long)chunk, W);
+        for (long long w = w0; w < w1; ++w) {
         const long long v = w * 32 + lane;
         uint64_t miss = 0;
         if (v < g.n) {
@@ -507,6 +525,7 @@ __device__ void ms_pull_level(const ParamsMS& p, const UnitView& g, MsLevel& L, 
                 (unsigned long long)(g.symmetric ? (end - beg) : (__ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v)));
             L.ef += dv;
             if (acc == miss) L.done_e += dv;  // no live lane misses v any more
+        }
         }
     }
 }
@@ -762,6 +781,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 ctl->slot[s].conv = 0;
                 ctl->slot[s].lanes = 0;
                 ctl->slot[s].done_e = 0;
+                ctl->slot[s].pull_next = 0;
             }
             ctl->slot[0].lanes = g.lanes;
         }
@@ -838,6 +858,7 @@ __device__ void msbfs_body(const ParamsMS& p) {
                 z->conv = 0;
                 z->lanes = 0;
                 z->done_e = 0;
+                z->pull_next = 0;
             }
             MsLevel L;
             L.level = level;
@@ -853,6 +874,9 @@ __device__ void msbfs_body(const ParamsMS& p) {
             L.done_e = 0;
             L.qbuf = sm.qbuf + warp * MS_QBUF;
             L.qn = 0;
+            L.cursor = &cur->pull_next;
+            // m_u: degree sum of the vertices some live lane has not seen
+            L.pull_chunk = 8 * m_u >= g.m ? MS_PULL_CHUNK_DENSE : MS_PULL_CHUNK_SPARSE;
             if (dir == BFS_DIR_PULL) ms_pull_level(p, g, L, sm, f_cur);
             else ms_push_level<T>(p, g, L, sm, a_cur, u_cur, f_cur, a, nunits);
             const uint64_t ln = warp_or64(L.lanes);
