@@ -161,6 +161,19 @@ enum {
                             memory) before expanding them */
 };
 
+/* Small levels of a single-source search (persistent drive).  While a push
+ * level's frontier is small, one thread-block cluster (16 CTAs where the GPU
+ * can co-schedule them, else 8) runs the levels with the cluster's hardware
+ * barrier instead of the grid-wide barrier; the first level that would pull
+ * or that has more frontier edges than the cluster's threads, and every level
+ * after it, runs in the full persistent kernel (a second launch on the same
+ * stream, no host round trip).  Sources run one launch pair each. */
+enum {
+    BFS_SMALL_AUTO = -1, /* on for graphs whose maximum degree is at most 64 (grids, road-like graphs) */
+    BFS_SMALL_OFF = 0,
+    BFS_SMALL_CLUSTER = 1
+};
+
 /* Per-level direction policy. */
 enum {
     BFS_POLICY_HEURISTIC = 0, /* Beamer: push->pull if e_f > m_u/alpha, pull->push if f < n/beta */
@@ -212,6 +225,8 @@ typedef struct {
     int32_t frontier_sort;   /* BFS_SORT_* (BFS_SORT_NONE); the CUDA-graph drive rejects a sort with EINVAL */
     float batch_alpha;       /* alpha of the 64-lane batched direction test (4) */
     float batch_beta;        /* beta of the 64-lane batched direction test (48) */
+    int32_t small_levels;    /* BFS_SMALL_* (BFS_SMALL_AUTO); single-source persistent drive with fused claiming
+                                and no frontier sort, else ignored */
 } bfs_options;
 
 /* Fill `opt` with the defaults listed above. */

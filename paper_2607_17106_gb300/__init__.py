@@ -33,6 +33,7 @@ BFS_MODE_PERSISTENT, BFS_MODE_HOST_LOOP, BFS_MODE_GRAPH = 0, 1, 2
 BFS_PUSH_FUSED, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED = 0, 1, 2
 # frontier order of push-queue levels
 BFS_SORT_NONE, BFS_SORT_DEVICE, BFS_SORT_TILE = 0, 1, 2
+BFS_SMALL_AUTO, BFS_SMALL_OFF, BFS_SMALL_CLUSTER = -1, 0, 1
 # policies
 BFS_POLICY_HEURISTIC, BFS_POLICY_PUSH, BFS_POLICY_PULL, BFS_POLICY_SCHEDULE, BFS_POLICY_MLP = range(5)
 BFS_MLP_IN, BFS_MLP_HIDDEN, BFS_MLP_OUT = 10, 32, 3
@@ -77,7 +78,7 @@ class bfs_options(ctypes.Structure):
                 ("level_log", ctypes.POINTER(bfs_level_record)), ("level_log_cap", ctypes.c_int32),
                 ("levels_out", ctypes.POINTER(ctypes.c_int32)), ("batch", ctypes.c_int32),
                 ("push_filter", ctypes.c_int32), ("frontier_sort", ctypes.c_int32),
-                ("batch_alpha", ctypes.c_float), ("batch_beta", ctypes.c_float)]
+                ("batch_alpha", ctypes.c_float), ("batch_beta", ctypes.c_float), ("small_levels", ctypes.c_int32)]
 
 
 _lib = None

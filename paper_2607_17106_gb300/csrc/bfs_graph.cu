@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(GT) g_bm2q(Params1 p) {
 template <int DIR>
 __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     __shared__ TileSmem<GT> sm;
+    __shared__ QueueStage<GT> qs;
     Ctl1* ctl = p.ctl;
     const GHead h = cta_head(ctl);
     const int level = h.level;
@@ -222,9 +223,10 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.next = nxt;
     L.ef = 0;
     L.cnt = 0;
-    L.qv = sm.t.qv + (threadIdx.x >> 5) * QBUF;
-    L.qb = sm.t.qb + (threadIdx.x >> 5) * QBUF;
-    L.qe = sm.t.qe + (threadIdx.x >> 5) * QBUF;
+    L.qv = qs.qv + (threadIdx.x >> 5) * QBUF;
+    L.qb = qs.qb + (threadIdx.x >> 5) * QBUF;
+    L.qe = qs.qe + (threadIdx.x >> 5) * QBUF;
+    L.qp = qs.qp + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
     L.qcap = p.n;
     L.err = &p.ctl->bar.err;

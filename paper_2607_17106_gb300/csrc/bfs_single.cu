@@ -69,12 +69,16 @@ void free_ws1(Workspace1* w) {
 
 // ------------------------------------------------------------ the kernel
 // Dynamic shared memory of the persistent kernel: the round list of the
-// list-driven pull (T * 32 16-bit entries), then a copy of the policy
-// weights, evaluated by every CTA at every level when the policy is the MLP.
+// list-driven pull (T * 32 16-bit entries; push levels use the same bytes
+// for the warps' next-queue staging, QueueStage<T>), then a copy of the
+// policy weights, evaluated by every CTA at every level when the policy is
+// the MLP.
 template <int T>
 constexpr size_t bfs1_list_bytes() {
+    static_assert(sizeof(QueueStage<T>) <= (size_t)T * 32 * sizeof(uint16_t), "staging fits the list bytes");
     return (size_t)T * 32 * sizeof(uint16_t);
 }
+
 template <int T>
 constexpr size_t bfs1_dyn_smem() {
     return bfs1_list_bytes<T>() + (size_t)NWEIGHTS * sizeof(float);
@@ -94,9 +98,32 @@ __device__ __forceinline__ void fill_minus1(int32_t* a, long long len, long long
     if (gtid < len - t0) a[t0 + gtid] = -1;
 }
 
+// The barrier between phases of a level.  A grid-wide launch uses the
+// %globaltimer-limited grid barrier; a launch of one thread-block cluster
+// (CL) uses the cluster's hardware barrier, whose arrive/wait orders every
+// thread's memory operations at cluster scope.  before_arrival and
+// after_open run on thread 0 as in grid_sync.
+template <bool CL, typename F = NoArrivalWork, typename A = NoArrivalWork>
+__device__ __forceinline__ bool level_sync(GridBarrier* b, unsigned nblocks, unsigned& target, int64_t timeout_ns,
+                                           F before_arrival = F(), A after_open = A()) {
+    if constexpr (CL) {
+        __syncthreads();
+        if (threadIdx.x == 0) before_arrival();
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        if (threadIdx.x == 0) after_open();
+        __syncthreads();
+        return true;
+    } else {
+        return grid_sync(b, nblocks, target, timeout_ns, before_arrival, after_open);
+    }
+}
+
 // SORT: the frontier-sort variants are compiled in (a separate instantiation,
 // so that the default kernel carries none of their registers).
-template <int T, bool SORT>
+// CL: one thread-block cluster runs the small levels of one search (see
+// bfs_options.small_levels) and leaves the first level that is not a small
+// push-queue level to the grid-wide launch that follows it.
+template <int T, bool SORT, bool CL>
 __device__ __forceinline__ void bfs1_body(const Params1& p) {
     __shared__ TileSmem<T> sm;
     __shared__ float s_feat[BFS_MLP_IN];
@@ -125,6 +152,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     // (s_cnt_ok), else read at the top of the level
     __shared__ unsigned long long s_cnt[3];
     const unsigned warp = threadIdx.x >> 5;
+    QueueStage<T>* const qs = reinterpret_cast<QueueStage<T>*>(bfs1_dyn);
     for (int si = 0; si < nsearch; ++si) {
     int32_t* const depth = p.depth + (int64_t)si * p.n;
     int32_t* const parent = p.parent ? p.parent + (int64_t)si * p.n : nullptr;
@@ -138,8 +166,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             if (w == p.W - 1 && (p.n & 31)) bits |= ~((1u << (p.n & 31)) - 1u);  // phantom vertices
             p.P[w] = bits;
         }
-        fill_minus1(depth, p.n, gtid, gthreads);
-        if (parent) fill_minus1(parent, p.n, gtid, gthreads);
+        if (!p.rows_filled) {
+            fill_minus1(depth, p.n, gtid, gthreads);
+            if (parent) fill_minus1(parent, p.n, gtid, gthreads);
+        }
         __syncthreads();  // the CTA's warps have read s_cnt of the previous search's last level
         if (threadIdx.x == 0) {
             // every CTA knows level 0's counters without reading them back
@@ -173,7 +203,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
                 ctl->f_prev = 0;
             }
         }
-        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+        if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
         // after the barrier: ordered after every -1 store of the rows
         if (gtid == 0) {
             depth[s] = 0;
@@ -233,8 +263,12 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             done = true;
             break;
         }
-        if (level > 0) m_u -= e_f;
-        int dir = decide_dir(p, level, f, e_f, m_u, f_prev, prev_dir, s_feat, &s_mlp_out, mlp_w);
+        const long long m_u_lvl = level > 0 ? m_u - e_f : m_u;
+        int dir = decide_dir(p, level, f, e_f, m_u_lvl, f_prev, prev_dir, s_feat, &s_mlp_out, mlp_w);
+        // a cluster launch leaves every level but a small push-queue level to
+        // the grid-wide launch (the state is saved as the loop exits)
+        if (CL && (dir != BFS_DIR_PUSH_QUEUE || e_f > p.small_ef_max || q_valid != level)) break;
+        m_u = m_u_lvl;
         if (gtid == 0 && p.log && level < p.log_cap) {
             bfs_level_record r;
             r.level = level;
@@ -253,21 +287,21 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         if ((dir != BFS_DIR_PUSH_QUEUE || sort_dev) && bm_valid != level) {
             // queue -> bitmap conversion of F_i
             for (long long w = gtid; w < p.W; w += gthreads) f_cur[w] = 0;
-            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             for (long long q = gtid; q < f; q += gthreads) {
                 const int v = __ldcg(q_cur + q).x;
                 atomicOr(f_cur + (v >> 5), 1u << (v & 31));
             }
-            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             bm_valid = level;
         }
         if (sort_dev) {
             // ordered bitmap -> queue of F_i; chunk units only when no push
             // level has made them (after pull levels)
             sort_count<T>(p, sm, f_cur);
-            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             sort_emit<T>(p, sm, f_cur, q_cur, u_cur, cur, q_valid != level);
-            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             const unsigned long long* const usrc[1] = {&cur->u_len};
             unsigned long long uv[1];
             cta_load_u64<1>(usrc, uv);
@@ -276,7 +310,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         } else if (dir == BFS_DIR_PUSH_QUEUE && q_valid != level) {
             // bitmap -> queue conversion of F_i (after pull levels)
             bitmap_to_queue<T>(p, sm, f_cur, q_cur, u_cur, cur);
-            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             const unsigned long long* const usrc[1] = {&cur->u_len};
             unsigned long long uv[1];
             cta_load_u64<1>(usrc, uv);
@@ -300,9 +334,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.next = nxt;
         L.ef = 0;
         L.cnt = 0;
-        L.qv = sm.t.qv + warp * QBUF;
-        L.qb = sm.t.qb + warp * QBUF;
-        L.qe = sm.t.qe + warp * QBUF;
+        L.qv = qs->qv + warp * QBUF;
+        L.qb = qs->qb + warp * QBUF;
+        L.qe = qs->qe + warp * QBUF;
+        L.qp = qs->qp + warp * QBUF;
         L.qn = 0;
         L.qcap = p.n;
         L.err = &p.ctl->bar.err;
@@ -313,7 +348,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             push_level<T, SORT>(p, L, sm, dir, q_cur, u_cur, f_cur, f, nunits, q_valid == level);
             if (p.push_filter != BFS_PUSH_FUSED) {
                 // the advance is complete everywhere before any pair is claimed
-                if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+                if (!level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
                 const unsigned long long* const esrc[1] = {&nxt->e_len};
                 unsigned long long ev[1];
                 cta_load_u64<1>(esrc, ev);
@@ -336,7 +371,7 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         f_prev = f;
         const int done_level = level;
         ++level;
-        const bool ok = grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns, [&]() {
+        const bool ok = level_sync<CL>(&ctl->bar, nblocks, bar_target, p.timeout_ns, [&]() {
             unsigned long long te = 0, tc = 0;
             for (int i = 0; i < T / 32; ++i) {
                 te += sm.red[i];
@@ -382,9 +417,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
 
 // At most 40 registers a thread for T <= 512, so that 1536 threads (48 warps
 // of memory-level parallelism for the latency-bound gathers) fit on an SM.
-template <int T, bool SORT>
+template <int T, bool SORT, bool CL = false>
 __global__ void __launch_bounds__(T, (1536 / T) > 0 ? (1536 / T) : 1) bfs1_kernel(Params1 p) {
-    bfs1_body<T, SORT>(p);
+    bfs1_body<T, SORT, CL>(p);
     if (threadIdx.x == 0) {
         int e = ld_volatile_i32(&p.ctl->bar.err);
         if (e) atomicCAS(p.sticky, 0, e);
@@ -417,6 +452,90 @@ int max_coop_blocks(int blocks_per_sm) {
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     return per_sm * num_sms();
+}
+
+// Small levels (bfs_options.small_levels): one cluster of 1024-thread CTAs,
+// 16 where the GPU can co-schedule such a cluster, else 8 (0: none).
+constexpr int SMALL_T = 1024;
+static int small_cluster_size() {
+    static int cached[64] = {};
+    const int d = device_id();
+    if (d < 0 || d >= 64) return 0;
+    if (cached[d]) return cached[d] > 0 ? cached[d] : 0;
+    int found = -1;
+    const size_t dyn = bfs1_dyn_smem<SMALL_T>();
+    auto k = bfs1_kernel<SMALL_T, false, true>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int cl : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cl);
+            cfg.blockDim = dim3(SMALL_T);
+            cfg.dynamicSmemBytes = dyn;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cl;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) == cudaSuccess && nc >= 1) {
+                found = cl;
+                break;
+            }
+        }
+    }
+    cudaGetLastError();  // an unsupported size leaves a non-sticky error
+    cached[d] = found;
+    return found > 0 ? found : 0;
+}
+
+static cudaError_t launch_small(const Params1& p, int cl, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(SMALL_T);
+    cfg.dynamicSmemBytes = bfs1_dyn_smem<SMALL_T>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bfs1_kernel<SMALL_T, false, true>, p);
+}
+
+// The cluster size to run a search's small levels with, 0 for none.  The
+// automatic choice takes graphs of bounded degree (grid- and road-like),
+// whose frontiers stay small for many levels; on ER-22 (maximum degree
+// about 40) the cluster's first levels and the second launch cost more
+// than the cheaper barrier saves.
+static int small_levels_for(const bfs_graph* g, const bfs_options& o) {
+    if (o.mode != BFS_MODE_PERSISTENT || o.frontier_sort != BFS_SORT_NONE || o.push_filter != BFS_PUSH_FUSED) return 0;
+    if (o.small_levels == BFS_SMALL_OFF) return 0;
+    if (o.small_levels == BFS_SMALL_AUTO && g->deg_max > 16) return 0;
+    return small_cluster_size();
+}
+
+// The small-level launch pair of one search: the -1 rows stored by the copy
+// engines' memset (the cluster's few SMs would take long to store them),
+// the cluster launch, then the grid-wide launch that finishes the search.
+template <typename L>
+static cudaError_t run_small_pair(Params1 q, int cl, const L& launcher, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(q.depth, 0xff, (size_t)q.n * sizeof(int32_t), st);
+    if (!e && q.parent) e = cudaMemsetAsync(q.parent, 0xff, (size_t)q.n * sizeof(int32_t), st);
+    q.do_init = 1;
+    q.level_count = INT32_MAX / 2;
+    q.small_ef_max = (int64_t)cl * SMALL_T;  // about one frontier edge a thread
+    q.rows_filled = 1;
+    if (!e) e = launch_small(q, cl, st);
+    q.do_init = 0;
+    q.small_ef_max = 0;
+    q.rows_filled = 0;
+    if (!e) e = launcher(q, st);
+    return e;
 }
 
 __global__ void count_units_kernel(const int32_t* row_ptr, int32_t n, int32_t chunk, unsigned long long* out) {
@@ -641,7 +760,13 @@ bfs_status run_single(bfs_graph* g, int32_t src_value, int32_t* depth, int32_t* 
     } else {
         p.do_init = 1;
         p.level_count = INT32_MAX / 2;
-        BFS_CUDA(launch(p));
+        if (const int cl = small_levels_for(g, o)) {
+            // the small levels in one cluster, the rest grid-wide (a launch
+            // that finds the search done returns at once)
+            BFS_CUDA(run_small_pair(p, cl, launcher, st));
+        } else {
+            BFS_CUDA(launch(p));
+        }
     }
     bool need_sync = o.level_log || o.levels_out || o.mode == BFS_MODE_HOST_LOOP;
     if (!need_sync) return BFS_OK;
@@ -688,10 +813,25 @@ bfs_status run_single_many(bfs_graph* g, const int32_t* src_host, int32_t k, int
     BFS_CUDA(cudaMemcpyAsync(w->d_srcs, src_host, (size_t)k * 4, cudaMemcpyHostToDevice, st));
     p.srcs = w->d_srcs;
     p.nsrc = k;
-    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
     CoopLauncher launcher(o);
     if (o.frontier_sort == BFS_SORT_DEVICE && launcher.blocks > 4096)
         return fail(BFS_EINVAL, "frontier_sort supports at most 4096 CTAs (launch has %d)", launcher.blocks);
+    if (const int cl = small_levels_for(g, o)) {
+        // a pair of launches per source: the small levels in one cluster,
+        // the rest grid-wide
+        for (int32_t si = 0; si < k; ++si) {
+            Params1 q = p;
+            q.srcs = nullptr;
+            q.nsrc = 1;
+            q.src_value = src_host[si];
+            q.depth = depth + (int64_t)si * g->n;
+            q.parent = parent ? parent + (int64_t)si * g->n : nullptr;
+            BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
+            BFS_CUDA(run_small_pair(q, cl, launcher, st));
+        }
+        return BFS_OK;
+    }
+    BFS_CUDA(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl1), st));
     p.do_init = 1;
     p.level_count = INT32_MAX / 2;
     BFS_CUDA(launcher(p, st));

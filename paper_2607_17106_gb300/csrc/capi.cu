@@ -97,6 +97,7 @@ extern "C" void bfs_options_init(bfs_options* o) {
     o->claim_aggregate = 0;
     o->push_filter = BFS_PUSH_FUSED;
     o->frontier_sort = BFS_SORT_NONE;
+    o->small_levels = BFS_SMALL_AUTO;
     o->barrier_timeout_ns = 2000000000ll;
     o->batch = 1;
 }
@@ -124,6 +125,8 @@ static bfs_status check_options(const bfs_options* in, bfs_options* o) {
         return fail(BFS_EINVAL, "bad frontier_sort %d", o->frontier_sort);
     if (o->frontier_sort != BFS_SORT_NONE && o->mode == BFS_MODE_GRAPH)
         return fail(BFS_EINVAL, "frontier_sort needs the persistent or host-loop drive");
+    if (o->small_levels < BFS_SMALL_AUTO || o->small_levels > BFS_SMALL_CLUSTER)
+        return fail(BFS_EINVAL, "bad small_levels %d", o->small_levels);
     return BFS_OK;
 }
 

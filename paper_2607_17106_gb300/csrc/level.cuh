@@ -119,6 +119,8 @@ struct Params1 {
     // launch control
     int32_t do_init;
     int32_t level_count;  // levels to run in this launch (host loop: 1)
+    int64_t small_ef_max; // cluster launch: leave before a level with more frontier edges (or a pull)
+    int32_t rows_filled;  // the -1 of the depth and parent rows was stored before the launch
 };
 
 // ------------------------------------------------------------- direction
@@ -193,8 +195,9 @@ struct LevelCtx {
     unsigned long long ef;  // this thread's share of e_f(F_{i+1})
     unsigned long long cnt; // this thread's share of |F_{i+1}| (pull levels)
     int32_t* qv;            // this warp's staging of next-queue entries (QBUF
-    int32_t* qb;            // each): vertex, row begin, row end
+    int32_t* qb;            // each): vertex, row begin, row end, parent
     int32_t* qe;
+    int32_t* qp;
     int qn;                 // entries staged (warp-uniform)
     long long qcap;         // capacity of q_next (n entries)
     int* err;               // device error word of the run
@@ -213,21 +216,26 @@ __device__ __forceinline__ bool push_precheck(long long m_u, long long m, long l
 }
 
 
-// Move the warp's staged queue entries to the next queue: one atomic per
-// flush instead of one per claiming round.  An entry carries its vertex's row
-// bounds (loaded when the vertex was claimed), so expanding it next level
-// needs no row-offset load.  Warp-uniform.
+// Move the warp's staged queue entries to the next queue, one atomic per
+// flush, and write their depth and parent.  An entry carries its vertex's
+// row bounds (loaded when the vertex was claimed), so expanding it next
+// level needs no row-offset load.  Warp-uniform.
 __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
     if (L.qn == 0) return;
-    unsigned lane = lane_id();
+    const unsigned lane = lane_id();
+    __syncwarp();
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&L.next->q_len, (unsigned long long)L.qn);
     base = __shfl_sync(0xffffffffu, base, 0);
-    __syncwarp();
     // a vertex is claimed once, so the queue never outgrows n; were that ever
     // broken, record the overflow instead of writing past the buffer
     if (base + (unsigned long long)L.qn <= (unsigned long long)L.qcap) {
-        for (int i = (int)lane; i < L.qn; i += 32) L.q_next[base + i] = make_int4(L.qv[i], L.qb[i], L.qe[i], 0);
+        for (int i = (int)lane; i < L.qn; i += 32) {
+            const int v = L.qv[i];
+            L.q_next[base + i] = make_int4(v, L.qb[i], L.qe[i], 0);
+            L.depth[v] = L.level + 1;
+            if (L.parent) L.parent[v] = L.qp[i];
+        }
     } else if (lane == 0) {
         atomicCAS(L.err, 0, (int)DEV_OVERFLOW);
     }
@@ -245,9 +253,9 @@ __device__ __forceinline__ void emit_units_warp(const Params1& p, int2* u_out, C
     append_units_warp(u_out, &c->u_len, p.ucap, &p.ctl->bar.err, big, v, deg, p.chunk);
 }
 
-// Record vertices claimed in a push level: depth/parent, staged next-queue
-// slot (with the row bounds rb..re of v), degree sum, chunk units for big
-// rows.  Warp-uniform call.
+// Record vertices claimed in a push level: staged next-queue slot (with the
+// row bounds rb..re of v and the parent u; flush_qbuf writes depth and
+// parent), degree sum, chunk units for big rows.  Warp-uniform call.
 __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int rb, int re) {
     unsigned cm = __ballot_sync(0xffffffffu, claimed);
     if (!cm) return;
@@ -259,8 +267,7 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
         L.qv[slot] = v;
         L.qb[slot] = rb;
         L.qe[slot] = re;
-        L.depth[v] = L.level + 1;
-        if (L.parent) L.parent[v] = u;
+        L.qp[slot] = u;
         L.ef += (unsigned long long)deg;
     }
     L.qn += c;
@@ -388,6 +395,15 @@ struct PullListSmem {
     unsigned nb[T];  // bits of F_{i+1} found in each slot's word
 };
 
+// The warps' staging of next-queue entries in push levels (QBUF each).
+template <int T>
+struct QueueStage {
+    int32_t qv[(T / 32) * QBUF];
+    int32_t qb[(T / 32) * QBUF];
+    int32_t qe[(T / 32) * QBUF];
+    int32_t qp[(T / 32) * QBUF];
+};
+
 // Shared memory of a CTA running level kernels.  Push levels use the tile
 // scratch and the warps' next-queue staging; pull levels use the round's
 // new-bit words; no level uses both, so they share storage.
@@ -399,9 +415,6 @@ struct TileSmem {
             int beg[T];
             int lim[T];
             int src[T];
-            int32_t qv[(T / 32) * QBUF];
-            int32_t qb[(T / 32) * QBUF];
-            int32_t qe[(T / 32) * QBUF];
         } t;
         PullListSmem<T> list;
     };

@@ -44,6 +44,7 @@ def test_options_layout_matches_c(lib):
     assert o.chunk == 1024 and o.block_threads == 1024 and o.batch == 1 and o.claim_aggregate == 0
     assert o.push_filter == bg.BFS_PUSH_FUSED
     assert o.frontier_sort == bg.BFS_SORT_NONE
+    assert o.small_levels == bg.BFS_SMALL_AUTO
     assert o.pull_serial == 16
     assert ctypes.sizeof(bg.bfs_level_record) == 40
     assert ctypes.sizeof(bg.bfs_graph_stats) == 48

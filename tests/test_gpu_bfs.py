@@ -337,22 +337,24 @@ def _barbell():
     return a + nr + b, src, dst
 
 
-@pytest.mark.parametrize("threads", [1024, 512])
-def test_long_runs_of_tiny_levels_around_a_burst(threads):
+@pytest.mark.parametrize("threads,small", [(1024, 0), (512, 0), (1024, 1), (512, 1)])
+def test_long_runs_of_tiny_levels_around_a_burst(threads, small):
     # thousands of one-vertex levels along the paths, two large levels in the
-    # RMAT component between them
+    # RMAT component between them; with small=1 one thread-block cluster runs
+    # the path levels until the burst and the grid-wide launch the rest
     n, s, d = _barbell()
     adj, g = _graph_pair(n, s, d)
     srcs = [0, n - 1, 3000 + 5, 1500]
+    sl = bg.BFS_SMALL_CLUSTER if small else bg.BFS_SMALL_OFF
     for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
-        dd, pp = _run(g, n, srcs, bg.options(batch=0, policy=pol, block_threads=threads))
+        dd, pp = _run(g, n, srcs, bg.options(batch=0, policy=pol, block_threads=threads, small_levels=sl))
         _check(adj, srcs, dd, pp)
-    # the level log covers every level
+    # the level log covers every level, across the two launches
     log = (bg.bfs_level_record * 8192)()
     nlev = bg.ctypes.c_int32(0)
     depth = np.empty(n, np.int32)
     g.run(np.array([0], np.int32), depth, None, bg.options(batch=0, level_log=log, level_log_cap=8192,
-                                                          levels_out=bg.ctypes.pointer(nlev)))
+                                                          levels_out=bg.ctypes.pointer(nlev), small_levels=sl))
     ref = oracle.level_stats(adj, depth)
     assert nlev.value == len(ref)
     for i in range(nlev.value):
@@ -360,10 +362,42 @@ def test_long_runs_of_tiny_levels_around_a_burst(threads):
     assert log[nlev.value].dir == -1
     # the level limit is enforced in the middle of the first path
     with pytest.raises(bg.BfsError) as e:
-        _run(g, n, [0], bg.options(batch=0, max_levels=100))
+        _run(g, n, [0], bg.options(batch=0, max_levels=100, small_levels=sl))
     assert e.value.status == bg.BFS_ERANGE
-    dd, pp = _run(g, n, [0], bg.options(batch=0))
+    dd, pp = _run(g, n, [0], bg.options(batch=0, small_levels=sl))
     _check(adj, [0], dd, pp)
+
+
+@pytest.mark.parametrize("small", [bg.BFS_SMALL_AUTO, bg.BFS_SMALL_CLUSTER, bg.BFS_SMALL_OFF])
+def test_small_levels_in_a_cluster_on_grids(small):
+    # a relabelled grid with deletions (maximum degree 4: the automatic choice
+    # runs it in one cluster), n not a multiple of 32, several sources in one
+    # call, an isolated source; and an ER graph whose levels outgrow the
+    # cluster after a few levels
+    n, s, d = graphgen.grid(97, 83, 0.1, seed=41)
+    adj, g = _graph_pair(n, s, d)
+    deg = np.diff(adj.row_ptr)
+    iso = np.flatnonzero(deg == 0)
+    srcs = graphgen.sample_sources(n, s, d, 5, seed=42).tolist() + ([int(iso[0])] if len(iso) else [])
+    dd, pp = _run(g, n, srcs, bg.options(batch=0, small_levels=small))
+    _check(adj, srcs, dd, pp)
+    g.free()
+    n2, s2, d2 = graphgen.erdos_renyi(20000, 80000, seed=43)
+    adj2, g2 = _graph_pair(n2, s2, d2)
+    srcs2 = graphgen.sample_sources(n2, s2, d2, 3, seed=44).tolist()
+    for pol in (bg.BFS_POLICY_HEURISTIC, bg.BFS_POLICY_PUSH):
+        dd, pp = _run(g2, n2, srcs2, bg.options(batch=0, small_levels=small, policy=pol))
+        _check(adj2, srcs2, dd, pp)
+    g2.free()
+
+
+def test_small_levels_option_errors():
+    n, s, d = graphgen.grid(16, 16, 0.0, seed=1)
+    g = bg.Graph.build(n, s, d)
+    with pytest.raises(bg.BfsError) as e:
+        _run(g, n, [0], bg.options(batch=0, small_levels=2))
+    assert e.value.status == bg.BFS_EINVAL
+    g.free()
 
 
 def test_many_searches_in_one_launch_match_the_oracle():
