@@ -226,7 +226,6 @@ __global__ void __launch_bounds__(GT, 2) g_push(Params1 p) {
     L.qv = qs.qv + (threadIdx.x >> 5) * QBUF;
     L.qb = qs.qb + (threadIdx.x >> 5) * QBUF;
     L.qe = qs.qe + (threadIdx.x >> 5) * QBUF;
-    L.qp = qs.qp + (threadIdx.x >> 5) * QBUF;
     L.qn = 0;
     L.qcap = p.n;
     L.err = &p.ctl->bar.err;

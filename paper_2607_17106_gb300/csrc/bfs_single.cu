@@ -98,6 +98,22 @@ __device__ __forceinline__ void fill_minus1(int32_t* a, long long len, long long
     if (gtid < len - t0) a[t0 + gtid] = -1;
 }
 
+// Address of `p` (this CTA's shared memory) in the cluster's CTA 0.
+template <typename X>
+__device__ __forceinline__ X* cluster_map_rank0(X* p) {
+    uint64_t r;
+    asm volatile("mapa.u64 %0, %1, 0;" : "=l"(r) : "l"((uint64_t)p));
+    return reinterpret_cast<X*>(r);
+}
+
+// A level counter read right after the level barrier: from L2 in a
+// grid-wide launch, through distributed shared memory in a cluster launch.
+template <bool CL>
+__device__ __forceinline__ unsigned long long ld_counter(const unsigned long long* a) {
+    if constexpr (CL) return *reinterpret_cast<const volatile unsigned long long*>(a);
+    else return ld_cg_u64(a);
+}
+
 // The barrier between phases of a level.  A grid-wide launch uses the
 // %globaltimer-limited grid barrier; a launch of one thread-block cluster
 // (CL) uses the cluster's hardware barrier, whose arrive/wait orders every
@@ -151,12 +167,16 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     // the init, or read by thread 0 right after the level barrier opens
     // (s_cnt_ok), else read at the top of the level
     __shared__ unsigned long long s_cnt[3];
+    // A cluster launch keeps the level counters in CTA 0's shared memory
+    // (reached by every CTA of the cluster through distributed shared
+    // memory) and copies them to the control block when it leaves.
+    __shared__ Counters s_ctr[3];
     const unsigned warp = threadIdx.x >> 5;
     QueueStage<T>* const qs = reinterpret_cast<QueueStage<T>*>(bfs1_dyn);
     for (int si = 0; si < nsearch; ++si) {
     int32_t* const depth = p.depth + (int64_t)si * p.n;
     int32_t* const parent = p.parent ? p.parent + (int64_t)si * p.n : nullptr;
-    Counters* const cs = ctl->slot + 3 * (si & 1);
+    Counters* const cs = CL ? cluster_map_rank0(s_ctr) : ctl->slot + 3 * (si & 1);
     bool s_cnt_ok = false;
     if (p.do_init) {
         const int s = p.srcs ? __ldg(p.srcs + si) : p.src_value;
@@ -263,12 +283,15 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
             done = true;
             break;
         }
-        const long long m_u_lvl = level > 0 ? m_u - e_f : m_u;
-        int dir = decide_dir(p, level, f, e_f, m_u_lvl, f_prev, prev_dir, s_feat, &s_mlp_out, mlp_w);
+        if (level > 0) m_u -= e_f;
+        int dir = decide_dir(p, level, f, e_f, m_u, f_prev, prev_dir, s_feat, &s_mlp_out, mlp_w);
         // a cluster launch leaves every level but a small push-queue level to
-        // the grid-wide launch (the state is saved as the loop exits)
-        if (CL && (dir != BFS_DIR_PUSH_QUEUE || e_f > p.small_ef_max || q_valid != level)) break;
-        m_u = m_u_lvl;
+        // the grid-wide launch (the state, m_u as it was before the level, is
+        // saved as the loop exits)
+        if (CL && (dir != BFS_DIR_PUSH_QUEUE || e_f > p.small_ef_max || q_valid != level)) {
+            if (level > 0) m_u += e_f;
+            break;
+        }
         if (gtid == 0 && p.log && level < p.log_cap) {
             bfs_level_record r;
             r.level = level;
@@ -337,7 +360,6 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         L.qv = qs->qv + warp * QBUF;
         L.qb = qs->qb + warp * QBUF;
         L.qe = qs->qe + warp * QBUF;
-        L.qp = qs->qp + warp * QBUF;
         L.qn = 0;
         L.qcap = p.n;
         L.err = &p.ctl->bar.err;
@@ -384,9 +406,9 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
                 atomicMax((unsigned long long*)&p.log[p.log_cap / 2 + done_level].t_ns, (unsigned long long)globaltimer_ns());
 #endif
         }, [&]() {
-            s_cnt[0] = ld_cg_u64(&nxt->q_len);
-            s_cnt[1] = ld_cg_u64(&nxt->u_len);
-            s_cnt[2] = ld_cg_u64(&nxt->e_f);
+            s_cnt[0] = ld_counter<CL>(&nxt->q_len);
+            s_cnt[1] = ld_counter<CL>(&nxt->u_len);
+            s_cnt[2] = ld_counter<CL>(&nxt->e_f);
         });
         if (!ok) return;
         // the next iteration reads them before any CTA can change them: the
@@ -403,6 +425,10 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
     // the next search's init may overwrite P, the queues and the other
     // counter set while slower CTAs are still leaving.
     }  // searches
+    if (CL && gtid == 0) {
+        // the grid-wide launch that continues the search reads them there
+        for (int k = 0; k < 3; ++k) ctl->slot[k] = s_ctr[k];
+    }
     if (gtid == 0) {
         ctl->next_level = level;
         ctl->prev_dir = prev_dir;

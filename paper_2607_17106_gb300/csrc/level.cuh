@@ -195,9 +195,8 @@ struct LevelCtx {
     unsigned long long ef;  // this thread's share of e_f(F_{i+1})
     unsigned long long cnt; // this thread's share of |F_{i+1}| (pull levels)
     int32_t* qv;            // this warp's staging of next-queue entries (QBUF
-    int32_t* qb;            // each): vertex, row begin, row end, parent
+    int32_t* qb;            // each): vertex, row begin, row end
     int32_t* qe;
-    int32_t* qp;
     int qn;                 // entries staged (warp-uniform)
     long long qcap;         // capacity of q_next (n entries)
     int* err;               // device error word of the run
@@ -216,8 +215,8 @@ __device__ __forceinline__ bool push_precheck(long long m_u, long long m, long l
 }
 
 
-// Move the warp's staged queue entries to the next queue, one atomic per
-// flush, and write their depth and parent.  An entry carries its vertex's
+// Move the warp's staged queue entries to the next queue: one atomic per
+// flush instead of one per claiming round.  An entry carries its vertex's
 // row bounds (loaded when the vertex was claimed), so expanding it next
 // level needs no row-offset load.  Warp-uniform.
 __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
@@ -231,10 +230,7 @@ __device__ __forceinline__ void flush_qbuf(LevelCtx& L) {
     // broken, record the overflow instead of writing past the buffer
     if (base + (unsigned long long)L.qn <= (unsigned long long)L.qcap) {
         for (int i = (int)lane; i < L.qn; i += 32) {
-            const int v = L.qv[i];
-            L.q_next[base + i] = make_int4(v, L.qb[i], L.qe[i], 0);
-            L.depth[v] = L.level + 1;
-            if (L.parent) L.parent[v] = L.qp[i];
+            L.q_next[base + i] = make_int4(L.qv[i], L.qb[i], L.qe[i], 0);
         }
     } else if (lane == 0) {
         atomicCAS(L.err, 0, (int)DEV_OVERFLOW);
@@ -253,9 +249,9 @@ __device__ __forceinline__ void emit_units_warp(const Params1& p, int2* u_out, C
     append_units_warp(u_out, &c->u_len, p.ucap, &p.ctl->bar.err, big, v, deg, p.chunk);
 }
 
-// Record vertices claimed in a push level: staged next-queue slot (with the
-// row bounds rb..re of v and the parent u; flush_qbuf writes depth and
-// parent), degree sum, chunk units for big rows.  Warp-uniform call.
+// Record vertices claimed in a push level: depth/parent, staged next-queue
+// slot (with the row bounds rb..re of v), degree sum, chunk units for big
+// rows.  Warp-uniform call.
 __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed, int v, int u, int rb, int re) {
     unsigned cm = __ballot_sync(0xffffffffu, claimed);
     if (!cm) return;
@@ -267,7 +263,8 @@ __device__ __forceinline__ void emit(const Params1& p, LevelCtx& L, bool claimed
         L.qv[slot] = v;
         L.qb[slot] = rb;
         L.qe[slot] = re;
-        L.qp[slot] = u;
+        L.depth[v] = L.level + 1;
+        if (L.parent) L.parent[v] = u;
         L.ef += (unsigned long long)deg;
     }
     L.qn += c;
@@ -401,7 +398,6 @@ struct QueueStage {
     int32_t qv[(T / 32) * QBUF];
     int32_t qb[(T / 32) * QBUF];
     int32_t qe[(T / 32) * QBUF];
-    int32_t qp[(T / 32) * QBUF];
 };
 
 // Shared memory of a CTA running level kernels.  Push levels use the tile
