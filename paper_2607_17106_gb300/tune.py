@@ -27,7 +27,8 @@ import sys
 import numpy as np
 
 from . import (BFS_MODE_GRAPH, BFS_MODE_PERSISTENT, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED, BFS_PUSH_FUSED,
-               BFS_SORT_DEVICE, BFS_SORT_NONE, BFS_SORT_TILE, Graph, options)
+               BFS_SMALL_AUTO, BFS_SMALL_CLUSTER, BFS_SMALL_OFF, BFS_SORT_DEVICE, BFS_SORT_NONE, BFS_SORT_TILE, Graph,
+               options)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(_HERE, "tune_cache.json")
@@ -41,6 +42,7 @@ SINGLE_SPACE = {
     "claim_aggregate": [0, 1],
     "push_filter": [BFS_PUSH_FUSED, BFS_PUSH_FILTER, BFS_PUSH_FILTER_PREDICATED],
     "frontier_sort": [BFS_SORT_NONE, BFS_SORT_DEVICE, BFS_SORT_TILE],
+    "small_levels": [BFS_SMALL_AUTO, BFS_SMALL_OFF, BFS_SMALL_CLUSTER],
     "alpha": [8.0, 14.0, 24.0],
     "beta": [12.0, 24.0, 48.0],
     "gamma": [8.0, 16.0, 64.0],
