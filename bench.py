@@ -171,6 +171,16 @@ def rcm_leg(bg, torch, n, src, dst, sources, depth, parent, depth_h, stream, edg
             "depth_equal_under_renaming": same}
 
 
+def small_levels_active(bg, opt, info) -> bool:
+    """Whether bfs_run drives each source's small levels in a thread-block
+    cluster (a launch pair per source) under these options: the library's
+    rule for the persistent drive (fused claiming, no frontier sort; the
+    automatic choice for maximum degree <= 16)."""
+    if opt.mode != bg.BFS_MODE_PERSISTENT or opt.frontier_sort != bg.BFS_SORT_NONE or opt.push_filter != bg.BFS_PUSH_FUSED:
+        return False
+    return opt.small_levels == bg.BFS_SMALL_CLUSTER or (opt.small_levels == bg.BFS_SMALL_AUTO and info.deg_max <= 16)
+
+
 def teps_edges(stats: np.ndarray) -> float:
     """Undirected edges with both ends reached = (sum of degrees over reached vertices) / 2."""
     return float(stats[:, 1].sum()) / 2.0
@@ -657,11 +667,18 @@ def main():
                   "excluded_tiny_components": int((~big).sum()),
                   "us_per_search_one_launch_each": float(one_ms.mean() * 1e3),
                   "timer": "one launch per search (untimed pass); searches reaching < 1000 edges excluded"}
-    roof = {"bound": "hbm", "kernel": "bfs1_kernel (persistent; one launch runs the k searches in turn)",
+    small = small_levels_active(bg, opt, info)
+    launches_per_step = 2 * k if small else 1
+    kernel = ("bfs1_kernel (per source: a one-cluster launch for the small levels, then the grid-wide launch; "
+              "figures per step of k searches)" if small else
+              "bfs1_kernel (persistent; one launch runs the k searches in turn)")
+    roof = {"bound": "hbm", "kernel": kernel,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-            "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS, "bytes_per_launch": step_bmin,
-            "searches_per_launch": k, "launch_us": mean_launch_s * 1e6,
-            "us_per_search": mean_launch_s * 1e6 / k, "traffic": recorded_traffic(w.name)}
+            "frac_of_nominal_8TBs": achieved / NOMINAL_HBM_GBS, "bytes_per_launch": step_bmin / launches_per_step,
+            "bytes_per_step": step_bmin, "searches_per_step": k, "launches_per_step": launches_per_step,
+            "launch_us": mean_launch_s * 1e6 / launches_per_step, "step_us": mean_launch_s * 1e6,
+            "us_per_search": mean_launch_s * 1e6 / k,
+            "traffic": None if small else recorded_traffic(w.name)}
 
     extra = {}
     if not args.no_extra:
@@ -821,7 +838,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR col array %d MB)" % (4 * info.m // 2**20),
                        "parallelism": f"replicas x{ws}", "policy": "Beamer alpha=14 beta=48 (batched: alpha=4 beta=48)"},
             "roofline": roof, "per_search": teps_stats, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clk, **extra,
         }
         print(json.dumps(line))

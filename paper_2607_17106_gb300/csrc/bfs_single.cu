@@ -18,8 +18,9 @@
 // paper's ping-pong Depths variants 11/12: P_i is only read, P_{i+1} only
 // grows) and appends d to the next queue.
 //
-// Pull levels own whole 32-vertex words: a warp handles one word of P, so the
-// new bits of P and of F_{i+1} are written with plain stores.
+// Pull levels own whole 32-vertex words: each CTA lists the unvisited
+// vertices of its words in shared memory, its warps scan them, and the new
+// bits of P and of F_{i+1} go out with plain stores by the words' owners.
 //
 // Load balance (push): vertices with degree >= `chunk` are split at claim time
 // into chunk-edge units that whole CTAs take round-robin; the rest of
@@ -31,7 +32,9 @@
 // grid barrier with a %globaltimer limit, and every CTA evaluates the same
 // direction decision from the same device counters, so there is no host
 // round trip per level.  The host-loop mode launches the same kernel once per
-// level and carries the loop state in device memory.
+// level and carries the loop state in device memory.  On bounded-degree
+// graphs a launch of one thread-block cluster runs the small levels first
+// and the grid-wide launch continues from its saved state.
 #include "level.cuh"
 
 #include <algorithm>

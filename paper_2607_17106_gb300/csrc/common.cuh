@@ -170,13 +170,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsi
                 }
             }
         }
-#ifndef BFS_BAR_POSTCHECK
-#define BFS_BAR_POSTCHECK 1
-#endif
         if (ok) after_open();
-#if BFS_BAR_POSTCHECK
         if (ld_volatile_i32(&b->abort)) ok = 0;
-#endif
         s_ok = ok;
     }
     __syncthreads();

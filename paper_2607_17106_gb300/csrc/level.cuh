@@ -374,7 +374,8 @@ __device__ void filter_level(const Params1& p, LevelCtx& L, long long len) {
     flush_qbuf(L);
 }
 
-// ------------------------------------------------------------ push tiles
+// ------------------------------------------------------------ shared memory
+// A warp's scratch in the word-based pull (pull_level, graph mode).
 struct PullWarpSmem {
     unsigned nb[32];                   // new bits of the block's words (slot = the word's lane)
     int lv[32], lj[32], le[32], lb[32], ls[32];  // deferred rows: vertex, next entry, end, row start, slot
@@ -401,8 +402,10 @@ struct QueueStage {
 };
 
 // Shared memory of a CTA running level kernels.  Push levels use the tile
-// scratch and the warps' next-queue staging; pull levels use the round's
-// new-bit words; no level uses both, so they share storage.
+// scratch (their next-queue staging is a QueueStage of its own: in the
+// persistent kernel it shares the pull list's dynamic shared memory); pull
+// levels use the round's new-bit words; no level uses both, so they share
+// storage.
 template <int T>
 struct TileSmem {
     union {
