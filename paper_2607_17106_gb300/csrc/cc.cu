@@ -22,6 +22,9 @@
 //     pushed its current label.  Rows of at least CC_CHUNK entries are fixed
 //     chunk units, listed once, whose CTA-wide minimum goes in with one
 //     atomicMin.
+// After each iteration the vertices of F_{i+1} shortcut their labels
+// (cc_jump), which leaves the fixed point unchanged and shortens the chains
+// a label travels along on long-diameter graphs.
 #include "common.cuh"
 
 #include <algorithm>
@@ -86,6 +89,29 @@ __device__ __forceinline__ void cc_relax(const ParamsCC& p, uint32_t* f_nxt, int
 // modulo a power of two, which keeps low bits) gave one warp 10x the mean work.
 __device__ __forceinline__ long long cc_word(const ParamsCC& p, long long i) {
     return (long long)(((unsigned long long)i * p.wmul) % (unsigned long long)p.W);
+}
+
+// Shortcut step after an iteration's relaxations (the pointer jumping of
+// Shiloach-Vishkin-style algorithms): every vertex of F_{i+1} takes the label
+// of the vertex its label names, label[v] <- min(label[v], label[label[v]]).
+// A label is always the id of a vertex of the same component and labels only
+// drop, so the fixed point is unchanged (each vertex's smallest component
+// id); the step lets a label travel through the vertex it names instead of
+// one edge per iteration, which on long-diameter graphs cuts the iteration
+// count.  A thread takes words of F_{i+1} in a grid stride.
+__device__ __forceinline__ void cc_jump(const ParamsCC& p, const uint32_t* f_nxt) {
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    for (long long w = gtid; w < p.W; w += gthreads) {
+        unsigned fw = __ldcg(f_nxt + w);
+        while (fw) {
+            const int v = (int)(w * 32 + __ffs(fw) - 1);
+            fw &= fw - 1;
+            const int l = __ldcg(p.label + v);
+            const int ll = __ldcg(p.label + l);
+            if (ll < l) atomicMin(p.label + v, ll);
+        }
+    }
 }
 
 // |F_{i+1}|: one atomic per CTA
@@ -258,6 +284,8 @@ __global__ void __launch_bounds__(CC_T, 1) cc_kernel(ParamsCC p) {
             cc_pull<CC_T>(p, f_cur, f_nxt, u_cur, (long long)min(cv[1], (unsigned long long)p.ucap), n_big, cnt);
             cc_count(nxt, cnt, s_red);
             if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+            cc_jump(p, f_nxt);
+            if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
             continue;
         }
 
@@ -324,6 +352,8 @@ __global__ void __launch_bounds__(CC_T, 1) cc_kernel(ParamsCC p) {
         }
 
         cc_count(nxt, cnt, s_red);
+        if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
+        cc_jump(p, f_nxt);
         if (!grid_sync(&ctl->bar, nblocks, bar_target, p.timeout_ns)) return;
     }
     if (gtid == 0) ctl->iters = it;
