@@ -66,3 +66,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
         warmup = 0
 
     assert bench.run_reference(Args()) == 0
+
+
+def test_launch_pairs_counted_where_small_levels_run_in_a_cluster():
+    # the bench's launch count follows the library's rule: a launch pair per
+    # source for bounded-degree graphs under the persistent drive, else one
+    # launch for all the sources of a step
+    import types
+    import paper_2607_17106_gb300 as bg
+    from paper_2607_17106_gb300 import build
+    build.build()  # bfs_options_init comes from the library (no GPU needed)
+    bg.load()
+    o = bg.options(batch=0)
+    grid_like, rmat_like = types.SimpleNamespace(deg_max=4), types.SimpleNamespace(deg_max=5000)
+    assert bench.small_levels_active(bg, o, grid_like)
+    assert not bench.small_levels_active(bg, o, rmat_like)
+    assert bench.small_levels_active(bg, bg.options(batch=0, small_levels=bg.BFS_SMALL_CLUSTER), rmat_like)
+    assert not bench.small_levels_active(bg, bg.options(batch=0, small_levels=bg.BFS_SMALL_OFF), grid_like)
+    assert not bench.small_levels_active(bg, bg.options(batch=0, mode=bg.BFS_MODE_GRAPH), grid_like)
+    assert not bench.small_levels_active(bg, bg.options(batch=0, frontier_sort=bg.BFS_SORT_TILE), grid_like)
+    assert not bench.small_levels_active(bg, bg.options(batch=0, push_filter=bg.BFS_PUSH_FILTER), grid_like)
