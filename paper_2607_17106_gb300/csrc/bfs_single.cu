@@ -442,6 +442,11 @@ __device__ __forceinline__ void bfs1_body(const Params1& p) {
         ctl->done = done ? 1 : 0;
         ctl->bar_base = bar_target;
     }
+    if constexpr (CL) {
+        // CTA 0's shared memory holds the counters the other CTAs read
+        // through distributed shared memory: no CTA leaves before all are done
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
 }
 
 // At most 40 registers a thread for T <= 512, so that 1536 threads (48 warps
