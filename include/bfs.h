@@ -169,7 +169,7 @@ enum {
  * after it, runs in the full persistent kernel (a second launch on the same
  * stream, no host round trip).  Sources run one launch pair each. */
 enum {
-    BFS_SMALL_AUTO = -1, /* on for graphs whose maximum degree is at most 64 (grids, road-like graphs) */
+    BFS_SMALL_AUTO = -1, /* on for graphs whose maximum degree is at most 16 (grids, road-like graphs) */
     BFS_SMALL_OFF = 0,
     BFS_SMALL_CLUSTER = 1
 };
